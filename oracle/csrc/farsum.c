@@ -1,0 +1,82 @@
+/* Far-field layer-potential sums by direct summation (oracle, FP64).
+ *
+ * Test infrastructure only: linked by the oracle's Python loader, never by
+ * the CUDA library.
+ *
+ * For each requested target i and each density sigma_r this evaluates the
+ * Nystrom far sums of Section 4 (the target-independent smooth rule over all
+ * sources outside Near(i)):
+ *
+ *   out[r][k][t] = sum_{j : patch(j) not in Near(i)} w_j K_k(x_i, y_j) sigma_r[j]
+ *
+ * for the kernels k = 0..3 = S, D, S', S''+D' of Section 3 (d = x - y):
+ *   S      = 1/(4 pi r)
+ *   D      = n_y.d/(4 pi r^3)
+ *   S'     = -n_x.d/(4 pi r^3)
+ *   S''+D' = [3 (n_x.d)((n_x - n_y).d)/r^2 - (1 - n_x.n_y)]/(4 pi r^3)
+ *
+ * Sources are the N nodes themselves (node j belongs to patch j / np).  A
+ * plain double loop, parallel over targets with OpenMP.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+int oracle_far_sums(int64_t N, int64_t np_, const double *X, const double *n,
+                    const double *w, const int64_t *near_ptr, const int32_t *near_patch,
+                    int nrhs, const double *sigma, int64_t ntgt, const int64_t *targets,
+                    double *out)
+{
+    const double four_pi = 4.0 * 3.14159265358979323846;
+    const int64_t npatch = N / np_;
+    int bad = 0;
+#pragma omp parallel
+    {
+        char *is_near = (char *)calloc((size_t)npatch, 1);
+        double *acc = (double *)malloc(sizeof(double) * 4 * (size_t)nrhs);
+        if (!is_near || !acc) {
+#pragma omp atomic write
+            bad = 1;
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t t = 0; t < ntgt; ++t) {
+            if (!is_near || !acc) continue;
+            const int64_t i = targets[t];
+            for (int64_t b = near_ptr[i]; b < near_ptr[i + 1]; ++b) is_near[near_patch[b]] = 1;
+            memset(acc, 0, sizeof(double) * 4 * (size_t)nrhs);
+            const double xi0 = X[3 * i], xi1 = X[3 * i + 1], xi2 = X[3 * i + 2];
+            const double nx0 = n[3 * i], nx1 = n[3 * i + 1], nx2 = n[3 * i + 2];
+            for (int64_t j = 0; j < N; ++j) {
+                if (is_near[j / np_]) continue;
+                const double d0 = xi0 - X[3 * j], d1 = xi1 - X[3 * j + 1], d2 = xi2 - X[3 * j + 2];
+                const double ny0 = n[3 * j], ny1 = n[3 * j + 1], ny2 = n[3 * j + 2];
+                const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                const double r = sqrt(r2);
+                const double g = 1.0 / (four_pi * r);
+                const double g3 = g / r2;
+                const double nxd = nx0 * d0 + nx1 * d1 + nx2 * d2;
+                const double nyd = ny0 * d0 + ny1 * d1 + ny2 * d2;
+                const double nxny = nx0 * ny0 + nx1 * ny1 + nx2 * ny2;
+                const double kS = g;
+                const double kD = nyd * g3;
+                const double kSp = -nxd * g3;
+                const double kSD = (3.0 * nxd * (nxd - nyd) / r2 - (1.0 - nxny)) * g3;
+                for (int r_ = 0; r_ < nrhs; ++r_) {
+                    const double q = w[j] * sigma[(int64_t)r_ * N + j];
+                    acc[4 * r_ + 0] += kS * q;
+                    acc[4 * r_ + 1] += kD * q;
+                    acc[4 * r_ + 2] += kSp * q;
+                    acc[4 * r_ + 3] += kSD * q;
+                }
+            }
+            for (int r_ = 0; r_ < nrhs; ++r_)
+                for (int k = 0; k < 4; ++k)
+                    out[((int64_t)r_ * 4 + k) * ntgt + t] = acc[4 * r_ + k];
+            for (int64_t b = near_ptr[i]; b < near_ptr[i + 1]; ++b) is_near[near_patch[b]] = 0;
+        }
+        free(is_near);
+        free(acc);
+    }
+    return bad ? -1 : 0;
+}

@@ -1,0 +1,62 @@
+"""Loader for the oracle's C far-sum routine (test infrastructure only).
+
+Compiles oracle/csrc/farsum.c with gcc (-O2 -fopenmp) into oracle/_build on
+first use, or when the source is newer than the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "csrc", "farsum.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle_far.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99",
+                               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.oracle_far_sums.restype = ctypes.c_int
+        lib.oracle_far_sums.argtypes = [
+            ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_void_p, ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def far_sums(geo, near_ptr, near_patch, sigma, targets=None) -> np.ndarray:
+    """Far sums of all four kernels: [nrhs, 4, ntargets] (kernel order S, D, S', S''+D')."""
+    lib = _load()
+    sig = np.ascontiguousarray(np.atleast_2d(sigma), dtype=np.float64)
+    nrhs = sig.shape[0]
+    if targets is None:
+        targets = np.arange(geo.N, dtype=np.int64)
+    targets = np.ascontiguousarray(targets, dtype=np.int64)
+    X = np.ascontiguousarray(geo.X)
+    n = np.ascontiguousarray(geo.n)
+    w = np.ascontiguousarray(geo.w)
+    ptr = np.ascontiguousarray(near_ptr, dtype=np.int64)
+    pl = np.ascontiguousarray(near_patch, dtype=np.int32)
+    out = np.zeros((nrhs, 4, len(targets)))
+    rc = lib.oracle_far_sums(geo.N, geo.np_, X.ctypes.data, n.ctypes.data, w.ctypes.data,
+                             ptr.ctypes.data, pl.ctypes.data, nrhs, sig.ctypes.data,
+                             len(targets), targets.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise MemoryError("oracle far sum could not allocate its work arrays")
+    return out

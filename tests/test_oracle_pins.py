@@ -1,0 +1,290 @@
+"""Pins of the FP64 oracle against closed forms, invariants and library solves.
+
+Every check here compares the oracle with something other than itself: a
+textbook value, an identity of potential theory, a per-pair identity that
+holds exactly on the unit sphere, a LAPACK solve, or the oracle's own
+convergence under refinement of its quadrature tolerance.
+"""
+import os
+from math import factorial
+
+import numpy as np
+import pytest
+
+from workloads import surfaces as S
+from workloads.configs import config
+from workloads.nodes import node_rule
+from workloads.rhs import y32
+
+from oracle.basis import NodalBasis, eval_basis
+from oracle.geometry import build_geometry
+from oracle.gmres import dense_matrix, gmres, solve_lb
+from oracle.layers import discretise
+from oracle import farsum
+from oracle.quadrature import kernel_values, build_corrections
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+WORKERS = min(8, os.cpu_count() or 1)
+
+
+def _golden_constants():
+    out = {}
+    for line in open(os.path.join(GOLD, "geometry_constants.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def _golden_spectrum():
+    rows = [list(map(float, l.split())) for l in open(os.path.join(GOLD, "sphere_spectrum.txt"))
+            if l.strip() and not l.startswith("#")]
+    return {int(r[0]): dict(zip(("S", "Sp", "D", "SD", "A3"), r[1:])) for r in rows}
+
+
+def _harmonic(l, X):
+    """A spherical harmonic of degree l as a harmonic polynomial restricted to the sphere."""
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    return {0: np.ones_like(x), 1: x.copy(), 2: x * y, 3: y32(X),
+            4: x ** 4 - 6 * x * x * y * y + y ** 4}[l]
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    s = S.icosphere(1, 6)
+    return discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0, eps_q=1e-11,
+                      workers=WORKERS)
+
+
+@pytest.fixture(scope="module")
+def ellipsoid():
+    s = S.ellipsoid((1.0, 1.5, 2.0), 1, 6)
+    return discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0, eps_q=1e-11,
+                      workers=WORKERS)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    w = config(1)
+    s = w.surface
+    return w, discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0, eps_q=w.eps_quad,
+                         workers=WORKERS)
+
+
+# --- node rule and basis (Section 4) ---------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_node_rule_exact_positive_inside(k):
+    uv, w = node_rule(k)
+    assert uv.shape == ((k + 1) * (k + 2) // 2, 2)
+    assert np.all(uv > 0) and np.all(uv.sum(1) < 1)
+    assert np.all(w > 0)
+    assert abs(w.sum() - 0.5) < 1e-15
+    for a in range(k + 1):
+        for b in range(k + 1 - a):
+            exact = factorial(a) * factorial(b) / factorial(a + b + 2)
+            assert abs(np.sum(w * uv[:, 0] ** a * uv[:, 1] ** b) - exact) < 1e-15
+
+
+def test_basis_orthonormal_and_derivatives():
+    k = 8
+    g, gw = np.polynomial.legendre.leggauss(14)
+    g = 0.5 * (g + 1)
+    gw = 0.5 * gw
+    a, b = np.meshgrid(g, g, indexing="ij")
+    wa, wb = np.meshgrid(gw, gw, indexing="ij")
+    u, v, ww = (a * (1 - b)).ravel(), b.ravel(), (wa * wb * (1 - b)).ravel()
+    P = eval_basis(k, u, v)
+    G = np.einsum("pi,pj,p->ij", P, P, ww)
+    assert np.abs(G - np.eye(len(G))).max() < 1e-13
+    _, pu, pv = eval_basis(k, u[:7], v[:7], derivs=True)
+    h = 1e-6
+    fu = (eval_basis(k, u[:7] + h, v[:7]) - eval_basis(k, u[:7] - h, v[:7])) / (2 * h)
+    fv = (eval_basis(k, u[:7], v[:7] + h) - eval_basis(k, u[:7], v[:7] - h)) / (2 * h)
+    assert np.abs(fu - pu).max() < 1e-5 and np.abs(fv - pv).max() < 1e-5
+    B = NodalBasis(k, node_rule(k)[0])
+    uu, vv = B.uv[:, 0], B.uv[:, 1]
+    f = uu ** 3 * vv ** 2 + 2 * uu * vv ** 5 - vv ** 8 + uu ** 8
+    assert np.abs(B.Du @ f - (3 * uu ** 2 * vv ** 2 + 2 * vv ** 5 + 8 * uu ** 7)).max() < 1e-12
+    assert np.abs(B.Dv @ f - (2 * uu ** 3 * vv + 10 * uu * vv ** 4 - 8 * vv ** 7)).max() < 1e-12
+
+
+# --- geometry (Sections 2 and 4) --------------------------------------------
+
+def _geo(s):
+    return build_geometry(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv)
+
+
+def test_geometry_closed_forms():
+    c = _golden_constants()
+    g = _geo(S.icosphere(2, 8))
+    assert abs(g.w.sum() - c["sphere_area"]) < 1e-9
+    assert abs(np.sum(g.w * np.einsum("ij,ij->i", g.X, g.n)) / 3 - c["sphere_volume"]) < 1e-9
+    assert np.abs(g.H - 1.0).max() < 1e-6
+    g = _geo(S.ellipsoid((1.0, 1.5, 2.0), 2, 8))
+    assert abs(np.sum(g.w * np.einsum("ij,ij->i", g.X, g.n)) / 3 - c["ellipsoid_volume"]) < 1e-8
+    # mean curvature of the ellipsoid x^2/a^2 + y^2/b^2 + z^2/c^2 = 1:
+    # H = |grad F|^-3 (..) in closed form via the implicit-surface formula
+    a, b, cc = 1.0, 1.5, 2.0
+    x, y, z = g.X.T
+    p = np.sqrt(x * x / a ** 4 + y * y / b ** 4 + z * z / cc ** 4)
+    Hex = (x * x / a ** 4 * (1 / b ** 2 + 1 / cc ** 2) + y * y / b ** 4 * (1 / a ** 2 + 1 / cc ** 2)
+           + z * z / cc ** 4 * (1 / a ** 2 + 1 / b ** 2)) / (2 * p ** 3)
+    assert np.abs(g.H - Hex).max() < 1e-5
+    R, r = 2.0, 0.75
+    g = _geo(S.torus(R, r, 16, 16, 6))
+    assert abs(g.w.sum() - c["torus_area"]) < 1e-10
+    assert abs(np.sum(g.w * np.einsum("ij,ij->i", g.X, g.n)) / 3 - c["torus_volume"]) < 1e-10
+    phi = np.arctan2(g.X[:, 2], np.hypot(g.X[:, 0], g.X[:, 1]) - R)
+    Hex = (R + 2 * r * np.cos(phi)) / (2 * r * (R + r * np.cos(phi)))
+    assert np.abs(g.H - Hex).max() < 1e-6
+    assert abs(np.sum(g.w * g.H) - c["torus_mean_curvature_integral"]) < 1e-6
+
+
+# --- kernels (Section 3) ---------------------------------------------------
+
+def test_kernels_unit_sphere_per_pair():
+    """On the unit sphere n.(x-y) = |x-y|^2/2, so per pair K_S' = K_D = -K_S/2, K_S''+D' = K_S."""
+    rng = np.random.default_rng(5)
+    P = rng.standard_normal((2, 200, 3))
+    P /= np.linalg.norm(P, axis=-1, keepdims=True)
+    K, _ = kernel_values(P[0], P[0], P[1], P[1])
+    assert np.allclose(K[:, 1], -0.5 * K[:, 0], rtol=1e-12, atol=0)
+    assert np.allclose(K[:, 2], -0.5 * K[:, 0], rtol=1e-12, atol=0)
+    assert np.allclose(K[:, 3], K[:, 0], rtol=1e-10, atol=0)
+
+
+def test_far_sums_unit_sphere_identities(sphere):
+    g = sphere.geo
+    rng = np.random.default_rng(7)
+    sig = rng.standard_normal((2, g.N))
+    F = farsum.far_sums(g, sphere.near_ptr, sphere.near_patch, sig)
+    scale = np.abs(F[:, 0]).max()
+    assert np.abs(F[:, 1] + 0.5 * F[:, 0]).max() < 1e-13 * scale * 100
+    assert np.abs(F[:, 2] + 0.5 * F[:, 0]).max() < 1e-13 * scale * 100
+    assert np.abs(F[:, 3] - F[:, 0]).max() < 1e-12 * scale * 100
+    # linearity and the subset of targets
+    t = np.array([0, 5, 17, g.N - 1])
+    Ft = farsum.far_sums(g, sphere.near_ptr, sphere.near_patch, sig, targets=t)
+    assert np.abs(Ft - F[:, :, t]).max() == 0.0
+
+
+# --- potentials: far + near (Sections 3, 4) --------------------------------
+
+@pytest.mark.parametrize("l", [0, 1, 2, 3, 4])
+def test_sphere_spectrum_of_potentials(sphere, l):
+    gold = _golden_spectrum()[l]
+    f = _harmonic(l, sphere.geo.X)
+    p = sphere.potentials(f)[0]
+    scale = np.abs(f).max()
+    for k, name in enumerate(("S", "D", "Sp", "SD")):
+        assert np.abs(p[k] - gold[name] * f).max() < 1e-4 * scale, name
+
+
+@pytest.mark.parametrize("l", [0, 1, 3, 4])
+@pytest.mark.parametrize("form", ["A3", "A2"])
+def test_sphere_spectrum_of_operators(sphere, l, form):
+    gold = _golden_spectrum()[l]["A3"]
+    f = _harmonic(l, sphere.geo.X)
+    Af = sphere.apply(form, f)[0]
+    assert np.abs(Af - gold * f).max() < 2e-3 * np.abs(f).max()
+
+
+def test_ellipsoid_gauss_green_adjoint(ellipsoid):
+    g = ellipsoid.geo
+    one = np.ones(g.N)
+    p = ellipsoid.potentials(one)[0]
+    assert np.abs(p[1] + 0.5).max() < 5e-5                      # Gauss: D[1] = -1/2
+    rng = np.random.default_rng(3)
+    sig = rng.standard_normal(g.N)
+    Sp = ellipsoid.potentials(sig)[0][2]
+    # int S'[sigma] = -1/2 int sigma (adjoint of Gauss)
+    assert abs(np.sum(g.w * Sp) + 0.5 * np.sum(g.w * sig)) < 1e-4 * np.sum(g.w * np.abs(sig))
+    # Green: S[dU/dn] - D[U] = U/2 for harmonic U = x_k
+    for kx in range(3):
+        lhs = ellipsoid.potentials(g.n[:, kx])[0][0] - ellipsoid.potentials(g.X[:, kx])[0][1]
+        assert np.abs(lhs - 0.5 * g.X[:, kx]).max() < 1e-4
+
+
+def test_near_weights_converge_with_tolerance(cfg1):
+    w, d = cfg1
+    rows = np.array([0, 7, 150, 299])
+    v1, _ = build_corrections(d.geo, d.near_ptr, d.near_patch, eps_q=1e-9, rows=rows)
+    v2, _ = build_corrections(d.geo, d.near_ptr, d.near_patch, eps_q=1e-13, rows=rows, m=10)
+    sel = np.isin(np.repeat(np.arange(d.geo.N), np.diff(d.near_ptr)), rows)
+    assert np.abs(v1[sel] - d.vals[sel]).max() < 1e-9
+    assert np.abs(v2[sel] - d.vals[sel]).max() < 1e-10
+
+
+# --- solves (Sections 3, 6) ------------------------------------------------
+
+@pytest.mark.parametrize("form", ["A3", "A2"])
+def test_config1_solve_matches_closed_form(cfg1, form):
+    w, d = cfg1
+    u, sigma, it, hist = solve_lb(d, w.f[0], form, tol=1e-12)
+    assert it <= 12 and hist[-1] < 1e-12
+    assert abs(np.sum(d.geo.w * u)) < 1e-12                      # mean zero (Lemma 1)
+    assert np.abs(u - w.extra["u_exact"]).max() < 5e-3           # coarse 20-patch mesh
+    A = dense_matrix(lambda x: d.apply(form, x), d.geo.N)
+    b = d.rhs(form, w.f[0])[0]
+    x = np.linalg.solve(A, b)
+    assert np.abs(x - sigma).max() < 1e-11 * np.abs(x).max() * np.linalg.cond(A)
+    ev = np.linalg.eigvals(A)
+    assert np.mean(np.abs(ev + 0.25) < 0.05) > 0.9               # Section 6.2 clustering
+
+
+def test_sphere_solve_refined(sphere):
+    f = y32(sphere.geo.X)
+    for form in ("A3", "A2"):
+        u, _, it, _ = solve_lb(sphere, f, form, tol=1e-10)
+        assert np.abs(u + f / 12).max() < 2e-5
+
+
+def test_manufactured_ellipsoid(ellipsoid):
+    """Delta_Gamma x_1 = -2 H n_1, so f = -2 H n_1 gives u = x_1 - mean(x_1)."""
+    g = ellipsoid.geo
+    f = -2.0 * g.H * g.n[:, 0]
+    uex = g.X[:, 0] - np.sum(g.w * g.X[:, 0]) / g.w.sum()
+    for form in ("A3", "A2"):
+        u, _, it, _ = solve_lb(ellipsoid, f, form, tol=1e-10)
+        assert it < 30
+        assert np.abs(u - uex).max() < 5e-4
+
+
+def test_gmres_matches_lapack_on_random_matrix():
+    rng = np.random.default_rng(11)
+    A = np.eye(80) * -0.25 + 0.05 * rng.standard_normal((80, 80))
+    b = rng.standard_normal(80)
+    x, it, hist = gmres(lambda v: A @ v, b, tol=1e-13, max_iter=80)
+    assert np.abs(x - np.linalg.solve(A, b)).max() < 1e-11
+
+
+# --- planted mistakes: each pin must notice a plausible error --------------
+
+def test_planted_sign_error_in_D_breaks_gauss(ellipsoid, monkeypatch):
+    from oracle import quadrature as Q
+    orig = Q.kernel_values
+
+    def wrong(x, nx, y, ny):
+        K, r3 = orig(x, nx, y, ny)
+        K = K.copy()
+        K[..., 1] *= -1.0
+        return K, r3
+    monkeypatch.setattr(Q, "kernel_values", wrong)
+    g = ellipsoid.geo
+    rows = np.arange(0, g.N, 97)
+    v, _ = Q.build_corrections(g, ellipsoid.near_ptr, ellipsoid.near_patch, eps_q=1e-8, rows=rows)
+    sel = np.isin(np.repeat(np.arange(g.N), np.diff(ellipsoid.near_ptr)), rows)
+    d = type(ellipsoid)(g, ellipsoid.near_ptr, ellipsoid.near_patch, np.where(sel[:, None, None], v, ellipsoid.vals),
+                        ellipsoid.eta, 1e-8)
+    p = d.potentials(np.ones(g.N), targets=rows)[0]
+    assert np.abs(p[1] + 0.5).max() > 1e-2
+
+
+def test_planted_missing_curvature_term_breaks_spectrum(sphere, monkeypatch):
+    import oracle.layers as L
+    f = _harmonic(3, sphere.geo.X)
+    monkeypatch.setattr(sphere.geo, "H", np.zeros(sphere.geo.N))
+    Af = sphere.apply_A3(f)[0]
+    assert np.abs(Af - _golden_spectrum()[3]["A3"] * f).max() > 1e-2
+    del L
