@@ -1,0 +1,358 @@
+"""Benchmark: Laplace-Beltrami solve throughput on one GB300 (or N replicas).
+
+Workload (the default, and the one every number below refers to): the
+ellipsoid with semi-axes (1, 1.5, 2), an icosahedron subdivided three times
+into 1280 curved triangular patches of order 8 (45 nodes each, N = 57,600),
+right-hand side f = a seeded sum of 8 Gaussian bumps exp(-|x - c_i|^2 / 0.1)
+centred on surface nodes, synthetic data.
+
+One step = one mean-zero Laplace-Beltrami solve Delta_Gamma u = f through the
+A3 formulation to relative residual 1e-10: float32 far-field pair sums inside
+float64 GMRES and float64 iterative refinement, near-field corrections built
+once before timing (the setup time t_q is reported separately).  The metric
+is far-field pair interactions evaluated per second during the solve
+(Ginteractions/s, every evaluated pair counted, float32 and float64 alike),
+next to the time to solve.
+
+Timing: W untimed warm-up solves, then K solves, each bracketed by CUDA
+events on the library's stream, with a 512 MB write between steps to flush
+the 129 MB L2; a barrier and a device synchronise bracket the K steps, and
+the maximum over ranks is reported.  Under torchrun every rank runs its own
+replica of the workload on its own GPU (the solve has no exchange step).
+
+--impl reference times the FP64 CPU oracle (tests' reference
+implementation) on the host cores instead: its far-field sums for an A3
+apply (one density, then two) on a bounded sample of target nodes.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Layer-potential apply Ginteractions/s; time-to-solve at 1e-10 rel. residual"
+UNIT = "Ginteractions/s"
+WORKLOAD = ("ellipsoid (1,1.5,2), 1280 order-8 patches (N=57,600), f = 8 Gaussian bumps; "
+            "A3 solve to 1e-10 rel. residual")
+
+# far-field flops per evaluated pair, counting an FMA as two (kernel source in
+# paper_2111_10743_gb300/csrc/far.cu): d (3), r^2 (5), then per kind
+FLOPS_PER_PAIR = {"k1": 20, "kall": 45, "k2": 43, "k4": 21}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2111_10743_gb300", "csrc", "far.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = t.get(kernel)
+    if not ent or ent.get("far_cu_sha256") != digest:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    import paper_2111_10743_gb300 as lb
+    from workloads.configs import config
+
+    w = config(2)
+    s = w.surface
+    prec = {"fp32_refined": lb.LB_FP32_REFINED, "fp64": lb.LB_FP64, "fp32": lb.LB_FP32}[args.precision]
+    params = lb.default_params(eps_quad=1e-12, tol=1e-10, precision=prec, formulation=lb.LB_A3)
+    stream = torch.cuda.current_stream()
+    ctx = lb.Context(local, params, stream=stream)
+    ctx.upload_surface(s)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ctx.build_corrections()
+    torch.cuda.synchronize()
+    t_q = time.time() - t0
+    f = torch.tensor(w.f, device="cuda")
+    u = torch.empty_like(f)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        _, info = ctx.solve_lb(f, out=u)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pairs = 0
+    infos = []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ctx.set_profiling(True)
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            _, info = ctx.solve_lb(f, out=u)
+            ev[k][1].record(stream)
+            pairs += info["pairs"]
+            infos.append(info)
+        torch.cuda.synchronize()
+        prof = ctx.get_profile()
+        ctx.set_profiling(False)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    clocks = clk.summary()
+
+    # end to end through the C ABI with pinned host buffers: copies inside
+    fh = torch.tensor(w.f).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    e2e_ms = []
+    for k in range(max(1, min(args.steps, 3))):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info_e = ctx.solve_lb(fh, out=uh)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_pairs = info_e["pairs"]
+
+    # worst rank
+    tot = torch.tensor([ms, sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
+    ms_max, e2e_max = float(tot[0]), float(tot[1])
+    if rank != 0:
+        return
+    ms_step = ms_max / args.steps
+    value = pairs * ws / (ms_max * 1e-3) / 1e9
+    e2e_value = e2e_pairs * ws / (e2e_max * 1e-3) / 1e9
+
+    # dominant far kernel: its flops per launch over its mean event-timed duration
+    peaks = _peaks()
+    sm_count = ctx.info()["sm_count"]
+    clk_mhz = clocks.get("sm_mhz") or (peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1440.0)
+    cats = {k: v for k, v in prof.items() if isinstance(v, dict) and k.startswith("far")}
+    dom = max(cats, key=lambda k: cats[k]["ms"]) if cats else None
+    roofline = None
+    if dom:
+        kind = dom.split("_")[1]
+        per_launch_ms = cats[dom]["ms"] / cats[dom]["calls"]
+        flops = s.N * s.N * FLOPS_PER_PAIR[kind]
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        if dom.startswith("far32"):
+            peak = sm_count * 128 * 2 * clk_mhz * 1e6 / 1e12
+            note = "fp32 CUDA-core FMA peak: SMs x 128 lanes x 2 flops x median SM clock sampled under load"
+        else:
+            peak = 1.25 * clk_mhz / 2070.0
+            note = "fp64 nominal 1.25 TFLOP/s scaled by median SM clock / 2070 MHz"
+        roofline = {"bound": "alu", "kernel": f"k_far<{dom}>", "achieved": round(achieved, 3),
+                    "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                    "traffic": _traffic(dom), "peak_source": note,
+                    "launch_ms": round(per_launch_ms, 4), "share_of_step": round(cats[dom]["ms"] / ms, 4)}
+    kernels = {k: {"ms_per_step": round(v["ms"] / args.steps, 3), "calls_per_step": v["calls"] / args.steps}
+               for k, v in prof.items() if isinstance(v, dict)}
+    last = infos[-1]
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs + f64 solve" if prec != lb.LB_FP64 else "f64",
+        "data": "synthetic", "time_to_solve_ms": round(ms_step, 3), "t_q_s": round(t_q, 2),
+        "config": {"workload": WORKLOAD, "N": s.N, "patches": s.npatch, "order": s.order,
+                   "formulation": "A3", "precision": args.precision, "tol": 1e-10, "eps_quad": 1e-12,
+                   "near_factor": 2.0, "l2": "512 MB write between timed steps",
+                   "parallelism": f"replicas x{ws}"},
+        "solve": {"iterations": last["iterations"], "refinements": last["refinements"],
+                  "applies_fp32": last["applies_fp32"], "applies_fp64": last["applies_fp64"],
+                  "rel_residual": last["rel_residual"], "pairs_per_step": last["pairs"]},
+        "kernels": kernels,
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "ms_per_step": round(e2e_max, 3),
+                "h2d_bytes_per_step": int(fh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8)},
+        "gpu_launches": int(prof["launches"]),
+        "clocks": clocks,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_targets)
+    print(json.dumps(out))
+
+
+def _oracle_step(geo, ptr, pl, rng_seed, targets):
+    from oracle import farsum
+    rng = np.random.default_rng(rng_seed)
+    tau = rng.standard_normal(geo.N)
+    mu = rng.standard_normal((2, geo.N))
+    t0 = time.perf_counter()
+    farsum.far_sums(geo, ptr, pl, tau, targets)       # pass 1: one density
+    farsum.far_sums(geo, ptr, pl, mu, targets)        # pass 2: two densities
+    dt = time.perf_counter() - t0
+    return dt, 3 * len(targets) * geo.N
+
+
+def _oracle_setup():
+    from oracle.geometry import build_geometry
+    from workloads.configs import config
+    w = config(2)
+    s = w.surface
+    geo = build_geometry(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv)
+    # near lists by the oracle's rule, vectorised over targets in chunks
+    N = geo.N
+    rows = []
+    for a in range(0, N, 4096):
+        d = np.linalg.norm(geo.X[a:a + 4096, None, :] - geo.centroid[None, :, :], axis=2)
+        rows += [np.nonzero(r < 2.0 * geo.radius)[0].astype(np.int32) for r in d]
+    ptr = np.zeros(N + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum([len(r) for r in rows])
+    return geo, ptr, np.concatenate(rows)
+
+
+def cpu_baseline(ntargets: int):
+    """The FP64 oracle's far sums on a bounded sample of targets, all host cores."""
+    geo, ptr, pl = _oracle_setup()
+    ntargets = ntargets or geo.N
+    targets = np.random.default_rng(7).choice(geo.N, ntargets, replace=False).astype(np.int64)
+    dt, inter = _oracle_step(geo, ptr, pl, 1, targets)
+    cores = os.cpu_count()
+    return {"value": round(inter / dt / 1e9, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"A3 apply far sums (1 + 2 densities, 4 kernels each) for {ntargets} sampled targets "
+                      f"x {geo.N} sources, FP64 C/OpenMP oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    geo, ptr, pl = _oracle_setup()
+    args.cpu_targets = args.cpu_targets or geo.N
+    targets = np.random.default_rng(7).choice(geo.N, args.cpu_targets, replace=False).astype(np.int64)
+    for k in range(args.warmup):
+        _oracle_step(geo, ptr, pl, 100 + k, targets[:64])
+    tot, inter = 0.0, 0
+    for k in range(args.steps):
+        dt, n = _oracle_step(geo, ptr, pl, k, targets)
+        tot += dt
+        inter += n
+    value = inter / tot / 1e9
+    cores = os.cpu_count()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": geo.N, "sample_targets": args.cpu_targets},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"A3 apply far sums for {args.cpu_targets} sampled targets x {geo.N} sources"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32_refined", choices=["fp32_refined", "fp64", "fp32"])
+    ap.add_argument("--cpu-targets", type=int, default=0, help="oracle sample size (0: every target)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/* gblb.h -- C ABI of the GB300 Laplace-Beltrami layer-potential library.
+ *
+ * The library discretises closed surfaces made of curved triangular patches
+ * (Section 4 of Agarwal, O'Neil & Rachh, "FMM-accelerated solvers for the
+ * Laplace-Beltrami problem on complex surfaces in three dimensions") and
+ * applies, on one CUDA device, the layer potentials S, D, S', S''+D' and
+ * grad S (Section 3), the second-kind operators A2 and A3 (Sections 4.2 and
+ * 4.3), and solves the mean-zero Laplace-Beltrami problem
+ * Delta_Gamma u = f (Section 2, Lemma 1) with GMRES (Section 6).  The Hodge
+ * decomposition of a tangential field into curl-free, divergence-free and
+ * harmonic parts (Section 5) is built on the solver.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: LB_OK (0) or a negative LB_E*
+ *     code.  A human-readable message for the last failure on a context is
+ *     returned by lb_last_error().  No C++ exception crosses this boundary.
+ *   - N = npatch * np nodes, patch-major: node index = patch * np + q, where
+ *     q indexes the reference nodes on T0 = {u, v >= 0, u + v <= 1}.
+ *   - Vectors over nodes are float64, contiguous.  A batch of nrhs vectors is
+ *     stored [nrhs][N].  Vector fields are [N][3] (or [nrhs][N][3]).
+ *   - Pointers marked "host or device" may point to host memory (pageable or
+ *     pinned) or to device memory of the context's device; the library looks
+ *     up the pointer kind and copies host data through its own device
+ *     buffers.  Pointers marked "device" must be device memory.
+ *   - All device work is enqueued on the context's stream (lb_set_stream);
+ *     entry points that return host-visible results (solve information,
+ *     host output buffers) synchronise that stream before returning.
+ *   - The caller keeps ownership of every pointer it passes; the library
+ *     copies what it needs.  The context owns all device memory it allocates
+ *     and frees it in lb_destroy().
+ *   - Contexts are not thread-safe: use one context per host thread.
+ */
+#ifndef GBLB_H
+#define GBLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LB_OK 0
+#define LB_EINVAL (-1)         /* bad argument (null pointer, size, non-finite input) */
+#define LB_ENOMEM (-2)         /* device or host allocation failed */
+#define LB_ECUDA (-3)          /* a CUDA runtime call failed */
+#define LB_ENOTCONVERGED (-4)  /* GMRES hit max_iter before tol; best iterate written */
+#define LB_ETIMEOUT (-5)       /* a bounded device-side wait expired */
+#define LB_EGEOM (-6)          /* degenerate geometry (zero Jacobian, bad node rule) */
+#define LB_ESTATE (-7)         /* call out of order (e.g. apply before geometry) */
+
+/* arithmetic of the far-field pair sums (the rest of the path is float64) */
+#define LB_FP64 0          /* float64 pairs */
+#define LB_FP32 1          /* float32 pairs, compensated accumulation */
+#define LB_FP32_REFINED 2  /* solve: float32 inner GMRES inside float64 refinement */
+
+/* integral-equation formulation (Section 4, Table 2) */
+#define LB_A2 2   /* u = S[sigma]:   -sigma/4 + D^2 - S(S''+D'+2HS') + SWS = S[f]  */
+#define LB_A3 3   /* u = S^2[sigma]: -sigma/4 + S'^2 - (S''+D'+2HS')S + WS^2 = f    */
+
+/* kernels of the near-field correction blocks, in storage order */
+#define LB_K_S 0
+#define LB_K_D 1
+#define LB_K_SP 2
+#define LB_K_SPPDP 3
+#define LB_NKERNELS 4
+
+typedef struct lb_ctx lb_ctx;   /* opaque */
+
+typedef struct {
+  double eps_quad;      /* near-field quadrature tolerance (Section 6: epsilon); default 1e-12 */
+  double near_factor;   /* eta: patch P is near node x when |x - c_P| < eta * R_P; default 2 */
+  int precision;        /* LB_FP64, LB_FP32 or LB_FP32_REFINED; default LB_FP64 */
+  int formulation;      /* LB_A3 or LB_A2; default LB_A3 */
+  int max_iter;         /* GMRES iteration cap (Section 6 caps at 100); default 100 */
+  double tol;           /* relative residual target |b - A x| / |b|; default 1e-10 */
+  double inner_tol;     /* LB_FP32_REFINED: inner GMRES relative tolerance; default 1e-5 */
+  int max_refine;       /* LB_FP32_REFINED: outer refinement steps cap; default 6 */
+} lb_params;
+
+typedef struct {
+  int32_t iterations;       /* total GMRES iterations (inner iterations when refined) */
+  int32_t refinements;      /* outer refinement steps (0 for a plain solve) */
+  int32_t converged;        /* 1 if every right-hand side reached tol */
+  int32_t applies_fp64;     /* operator applies with float64 pair sums */
+  int32_t applies_fp32;     /* operator applies with float32 pair sums */
+  int32_t nrhs;
+  double rel_residual;      /* worst final relative residual over the batch (float64 apply) */
+  double removed_mean;      /* weighted mean removed from the first right-hand side */
+  double history[128];      /* relative residual estimate per GMRES iteration, first rhs */
+  int32_t history_len;
+  int64_t pairs;            /* far-field pair interactions evaluated by the solve */
+} lb_solve_info;
+
+typedef struct {
+  int64_t N;            /* number of nodes */
+  int64_t npatch;
+  int32_t np;           /* nodes per patch, (order+1)(order+2)/2 */
+  int32_t order;        /* total degree of the patch polynomials */
+  int64_t nnzb;         /* near (row, patch) blocks; 0 before near lists exist */
+  double area;          /* sum of the smooth weights */
+  int32_t sm_count;     /* multiprocessors of the device */
+  int32_t corrections;  /* 1 when correction blocks are present */
+} lb_geom_info;
+
+/* Fill *p with the defaults listed above. */
+int lb_default_params(lb_params* p);
+
+/* Create a context on CUDA device `device` with parameters *p (NULL: defaults).
+ * *out receives the context.  Errors: LB_EINVAL, LB_ECUDA, LB_ENOMEM. */
+int lb_create(lb_ctx** out, int device, const lb_params* p);
+
+/* Release every device buffer of the context and the context itself.
+ * Accepts NULL. */
+int lb_destroy(lb_ctx* ctx);
+
+/* Message for the last failing call on ctx (static string when ctx is NULL). */
+const char* lb_last_error(const lb_ctx* ctx);
+
+/* Replace the solver parameters.  Changing eps_quad or near_factor drops the
+ * near lists and corrections, which must then be rebuilt. */
+int lb_set_params(lb_ctx* ctx, const lb_params* p);
+int lb_get_params(const lb_ctx* ctx, lb_params* p);
+
+/* Enqueue all later work on `stream` (a cudaStream_t, NULL = legacy default). */
+int lb_set_stream(lb_ctx* ctx, void* stream);
+
+/* Upload a surface (Section 4: charts X^j : T0 -> Gamma_j sampled at an
+ * order-`order` node rule).
+ *   ref_uv [np][2], ref_w [np]: reference nodes and smooth weights on T0
+ *     (host or device); np must equal (order+1)(order+2)/2 and sum(ref_w)
+ *     must be 1/2.
+ *   X, Xu, Xv [N][3]: chart samples and their u/v derivatives (host or device),
+ *     oriented so that Xu x Xv points outward.
+ * Computes on the device (Sections 2 and 4): unit normals, weights
+ * w = ref_w |Xu x Xv|, the inverse metric, the mean curvature
+ * H = -1/2 tr(g^-1 L) from nodal differentiation of Xu and Xv, patch
+ * centroids and radii.  Drops earlier near lists and corrections.
+ * Errors: LB_EINVAL (sizes, node rule), LB_EGEOM (|Xu x Xv| = 0), LB_ENOMEM. */
+int lb_upload_geometry(lb_ctx* ctx, int64_t npatch, int order, const double* ref_uv,
+                       const double* ref_w, const double* X, const double* Xu,
+                       const double* Xv);
+
+/* Copy the derived node quantities to caller buffers (host or device; any may
+ * be NULL): normals n [N][3], weights w [N], mean curvature H [N]. */
+int lb_get_geometry(lb_ctx* ctx, double* n, double* w, double* H);
+
+int lb_geometry_info(lb_ctx* ctx, lb_geom_info* info);
+
+/* Build the near lists Near(i) = {P : |x_i - c_P| < eta R_P} (Section 4,
+ * the Near/Far split) on the device. */
+int lb_build_near(lb_ctx* ctx);
+
+/* Build the near-field correction blocks (Section 4, the corrected weights
+ * w~_ij composed with polynomial interpolation on each near patch): for
+ * every row i and P in Near(i), W^K_{i,P}[q] = int_P K(x_i, y) l_q(y) da(y)
+ * for K in {S, D, S', S''+D'}, by adaptive quadrature on the device (Duffy
+ * maps on the self patch, 1-to-4 subdivision on the others) to eps_quad.
+ * Builds the near lists first if needed.  This is the setup cost t_q of
+ * Section 6, amortised over the solve. */
+int lb_build_corrections(lb_ctx* ctx);
+
+/* Load externally computed near lists and correction blocks instead of
+ * building them (host or device pointers):
+ *   row_ptr [N+1] (int64): blocks of row i are row_ptr[i] .. row_ptr[i+1]-1,
+ *   patch [nnzb] (int32): the near patch of each block, ascending per row,
+ *   vals [nnzb][4][np] (float64): the weights, kernel order S, D, S', S''+D'.
+ * The far-field sums skip exactly these (row, patch) pairs. */
+int lb_load_corrections(lb_ctx* ctx, int64_t nnzb, const int64_t* row_ptr,
+                        const int32_t* patch, const double* vals);
+
+/* Copy the current near lists / corrections out (host or device buffers of
+ * the sizes above; vals may be NULL to fetch the lists only). */
+int lb_get_corrections(lb_ctx* ctx, int64_t* row_ptr, int32_t* patch, double* vals);
+
+/* Far-field sums alone (Section 4: the target-independent smooth rule over
+ * all sources outside Near(i)): out [nrhs][4][N] (host or device) receives
+ * sum_{j far} w_j K(x_i, x_j) sigma_j for K = S, D, S', S''+D', computed with
+ * `precision` (LB_FP64 or LB_FP32).  sigma [nrhs][N] host or device. */
+int lb_far_sums(lb_ctx* ctx, int precision, int nrhs, const double* sigma, double* out);
+
+/* Discretised potentials, far sum + near corrections (Section 4):
+ * out [nrhs][N] = K[sigma] for K = S, S', D, S''+D'.  sigma, out: host or
+ * device.  Far pairs use the context's precision (FP32_REFINED -> FP32). */
+int lb_apply_S(lb_ctx* ctx, int nrhs, const double* sigma, double* out);
+int lb_apply_Sp(lb_ctx* ctx, int nrhs, const double* sigma, double* out);
+int lb_apply_D(lb_ctx* ctx, int nrhs, const double* sigma, double* out);
+int lb_apply_SppDp(lb_ctx* ctx, int nrhs, const double* sigma, double* out);
+
+/* grad S on Gamma: out [nrhs][N][3] = n S'[sigma] + grad_Gamma S[sigma]
+ * (the principal-value gradient: normal part S', tangential part the surface
+ * gradient of the continuous potential S[sigma], by nodal differentiation
+ * within each patch, Section 2). */
+int lb_apply_gradS(lb_ctx* ctx, int nrhs, const double* sigma, double* out);
+
+/* The operator of the context's formulation (A3 or A2; Sections 4.2, 4.3):
+ * out [nrhs][N] = A tau.  tau, out: host or device. */
+int lb_apply_A(lb_ctx* ctx, int nrhs, const double* tau, double* out);
+
+/* Solve Delta_Gamma u = f for mean-zero u (Lemma 1), nrhs right-hand sides
+ * at once: f is projected to weighted mean zero, GMRES (x0 = 0, no restart,
+ * Euclidean norm, at most max_iter iterations) solves A sigma = b with
+ * b = f (A3) or b = S[f] (A2), and u = S[S[sigma]] (A3) or S[sigma] (A2).
+ * f, u [nrhs][N]: host or device.  info may be NULL.
+ * Precision LB_FP32_REFINED runs float32 inner GMRES inside a float64
+ * iterative refinement of the residual b - A sigma.
+ * Returns LB_ENOTCONVERGED (with u from the best iterate) when tol is not
+ * reached. */
+int lb_solve_lb(lb_ctx* ctx, int nrhs, const double* f, double* u, lb_solve_info* info);
+
+/* Harmonic vector fields (Section 5).  For each tangential field F_k
+ * (F [nF][N][3], host or device) solve
+ *   Delta alpha = div_Gamma F,   Delta beta = -div_Gamma (n x F)
+ * as one batch of 2 nF right-hand sides, then
+ *   H_k = F_k - grad_Gamma alpha - n x grad_Gamma beta
+ * and write H [2 nF][N][3] = (H_1, n x H_1, H_2, n x H_2, ...).  Surface
+ * divergence and gradient use nodal differentiation within each patch
+ * (Section 2).  info may be NULL. */
+int lb_harmonic_fields(lb_ctx* ctx, int nF, const double* F, double* H, lb_solve_info* info);
+
+/* Per-kernel device timing (CUDA events on the context stream) and kernel
+ * launch counts, for reporting the split of a solve into its steps.  Not in
+ * the paper, whose timings are wall-clock t_q, t_mv, t_s (Section 6). */
+#define LB_PROF_FAR32_K1 0     /* float32 charge potential + gradient (S, S', A3 pass 1) */
+#define LB_PROF_FAR32_KALL 1   /* float32 S, D, S', S''+D' of one density (A2 pass 1) */
+#define LB_PROF_FAR32_K2 2     /* float32 A3 pass 2 */
+#define LB_PROF_FAR32_K4 3     /* float32 A2 pass 2 */
+#define LB_PROF_FAR64_K1 4     /* the same four in float64 */
+#define LB_PROF_FAR64_KALL 5
+#define LB_PROF_FAR64_K2 6
+#define LB_PROF_FAR64_K4 7
+#define LB_PROF_EPILOGUE 8     /* split reduction + near-field correction SpMV */
+#define LB_PROF_QUAD 9         /* correction build */
+#define LB_PROF_NCAT 16
+
+typedef struct {
+  double ms[LB_PROF_NCAT];     /* summed device time per category */
+  int64_t calls[LB_PROF_NCAT]; /* timed launches per category */
+  int64_t launches;            /* every kernel launched while profiling was on */
+} lb_profile;
+
+/* Turn per-kernel timing on (1) or off (0); either way the counters restart. */
+int lb_set_profiling(lb_ctx* ctx, int on);
+/* Synchronise the context stream and return the counters since the last
+ * lb_set_profiling. */
+int lb_get_profile(lb_ctx* ctx, lb_profile* out);
+
+/* Surface divergence of tangential fields F [nrhs][N][3] -> out [nrhs][N]
+ * (Section 2; host or device).  Used for the Hodge right-hand sides and to
+ * check harmonic fields (div H = 0). */
+int lb_surface_div(lb_ctx* ctx, int nrhs, const double* F, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBLB_H */

@@ -92,6 +92,57 @@ def eval_basis(k: int, u, v, derivs: bool = False):
     return phi, np.moveaxis(phu, 0, -1), np.moveaxis(phv, 0, -1)
 
 
+def eval_basis_diff(k: int, ua: float, va: float, du, dv):
+    """Basis at p = a + (du, dv) together with phi_b(p) - phi_b(a), free of cancellation.
+
+    The differences are carried through the same recurrences with the product
+    rule  D(PQ) = DP Q(p) + P(a) DQ, starting from D u = du, D v = dv, so that
+    they keep full relative accuracy when p is close to a.  Returns
+    (phi(p), phi_u(p), phi_v(p), dphi) with shapes [P, n_p].
+    """
+    du = np.asarray(du, dtype=np.float64)
+    dv = np.asarray(dv, dtype=np.float64)
+    u = ua + du
+    v = va + dv
+    phi, phu, phv = eval_basis(k, u, v, derivs=True)
+    # values at a (scalars) and differences (arrays)
+    sa, sp = 1.0 - va, 1.0 - v
+    ds = -dv
+    A1a, A1p, dA1 = 2.0 * ua - sa, 2.0 * u - sp, 2.0 * du + dv
+    Aa = [1.0, A1a]
+    Ap = [np.ones_like(u), A1p]
+    dA = [np.zeros_like(u), dA1]
+    ds2 = ds * (sp + sa)
+    for j in range(1, k):
+        c1, c2 = 2 * j + 1, j
+        Aa.append((c1 * A1a * Aa[j] - c2 * sa * sa * Aa[j - 1]) / (j + 1))
+        Ap.append((c1 * A1p * Ap[j] - c2 * sp * sp * Ap[j - 1]) / (j + 1))
+        d_prod = dA1 * Ap[j] + A1a * dA[j]
+        d_s2A = ds2 * Ap[j - 1] + sa * sa * dA[j - 1]
+        dA.append((c1 * d_prod - c2 * d_s2A) / (j + 1))
+    xa, xp, dx = 2.0 * va - 1.0, 2.0 * v - 1.0, 2.0 * dv
+    out = np.empty(u.shape + ((k + 1) * (k + 2) // 2,))
+    col = 0
+    for n in range(k + 1):
+        al = 2.0 * n + 1.0
+        Pa = [1.0, 0.5 * ((al + 2.0) * xa + al)]
+        Pp = [np.ones_like(u), 0.5 * ((al + 2.0) * xp + al)]
+        dP = [np.zeros_like(u), 0.5 * (al + 2.0) * dx]
+        for m in range(2, k - n + 1):
+            c0 = 2.0 * m * (m + al) * (2 * m + al - 2)
+            ca = (2 * m + al - 1) * (2 * m + al) * (2 * m + al - 2)
+            cb = (2 * m + al - 1) * al * al
+            cc = 2.0 * (m + al - 1) * (m - 1) * (2 * m + al)
+            Pa.append(((ca * xa + cb) * Pa[m - 1] - cc * Pa[m - 2]) / c0)
+            Pp.append(((ca * xp + cb) * Pp[m - 1] - cc * Pp[m - 2]) / c0)
+            dP.append((ca * dx * Pp[m - 1] + (ca * xa + cb) * dP[m - 1] - cc * dP[m - 2]) / c0)
+        for m in range(k + 1 - n):
+            c = np.sqrt(2.0 * (2 * n + 1) * (n + m + 1))
+            out[..., col] = c * (dA[n] * Pp[m] + Aa[n] * dP[m])
+            col += 1
+    return phi, phu, phv, out
+
+
 class NodalBasis:
     """Interpolation and differentiation on T0 for a given node set."""
 

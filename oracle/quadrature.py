@@ -19,10 +19,17 @@ Integration follows Section 4's split:
     collapsed Gauss-Legendre rule on each triangle.
 A cell is accepted when its four children change its estimate by at most
 max(tol, floor) in every entry, and the children's sum is kept.  Here
-tol = eps_q * A_P / (4 pi R_P) (A_P the patch area, R_P its radius) and floor
-= 16 eps_mach (|x| + 2 R_P) sum_cell omega J / (4 pi r^3) bounds the rounding
-error of the O(r^2) numerators n.d near the target, below which refinement
-cannot improve the estimate.
+tol = eps_q * A_P / (4 pi R_P) (A_P the patch area, R_P its radius) and
+floor = 64 eps_mach sum_cell omega J max_q |l_q| rho bounds the rounding of
+the numerators n.d (each weighted by the largest interpolation weight at the
+point), below which refinement cannot improve the estimate.  On other
+patches d = x - y carries eps (|x| + 2 R_P) rounding, rho = (|x| + 2 R_P) /
+(4 pi r^3).  On the self patch d = y(a) - y(p) is formed from basis
+differences phi_b(p) - phi_b(a) carried through the basis recurrences, so it
+keeps full relative accuracy next to the target, and rho = 1 / (4 pi r^2).  A cell whose children sum is below tol in every entry is also
+accepted: its whole contribution is within the tolerance (this ends the
+refinement of the vanishing cells next to the Duffy apex).  At most
+max_cells cells per pair are refined (the rest are accepted and counted).
 
 Every quadrature point y is on the interpolated chart y = sum_q X_q l_q
 (Section 4).  Its tangents are the derivatives of that same polynomial, which
@@ -49,7 +56,7 @@ from __future__ import annotations
 import numpy as np
 from scipy.special import roots_legendre
 
-from .basis import eval_basis
+from .basis import eval_basis, eval_basis_diff
 from .geometry import Geometry
 
 KERNELS = ("S", "D", "Sp", "SppDp")
@@ -58,7 +65,11 @@ FOUR_PI = 4.0 * np.pi
 
 def kernel_values(x, nx, y, ny):
     """All four kernels for target/source pairs; inputs broadcast to [..., 3]."""
-    d = x - y
+    return kernel_values_d(x - y, nx, ny)
+
+
+def kernel_values_d(d, nx, ny):
+    """All four kernels from d = x - y; returns (K [..., 4], 1/(4 pi r^3))."""
     r2 = np.sum(d * d, axis=-1)
     r = np.sqrt(r2)
     inv4pir = 1.0 / (FOUR_PI * r)
@@ -102,12 +113,22 @@ class _PatchChart:
         J = np.linalg.norm(c, axis=-1)
         return y, c / J[:, None], J, phi @ self.Vinv
 
+    def at_offset(self, ua, va, du, dv):
+        """Chart at p = a + (du, dv) with y(a) - y(p) from basis differences."""
+        phi, phu, phv, dphi = eval_basis_diff(self.k, ua, va, du, dv)
+        d = -(dphi @ self.cX)
+        c = np.cross(phu @ self.cX, phv @ self.cX)
+        J = np.linalg.norm(c, axis=-1)
+        return d, c / J[:, None], J, phi @ self.Vinv
+
 
 class NearQuadrature:
-    def __init__(self, geo: Geometry, eps_q: float = 1e-12, m: int = 8, max_depth: int = 30):
+    def __init__(self, geo: Geometry, eps_q: float = 1e-12, m: int = 8, max_depth: int = 30,
+                 max_cells: int = 200000):
         self.geo = geo
         self.eps_q = eps_q
         self.max_depth = max_depth
+        self.max_cells = max_cells
         g, gw = roots_legendre(m)
         self.gx = 0.5 * (g + 1.0)
         self.gw = 0.5 * gw
@@ -116,7 +137,7 @@ class NearQuadrature:
     # --- cells -----------------------------------------------------------
     # a cell: target slot, triangle (a, b, c) in T0, rectangle [s0,s1]x[t0,t1]
     # of the Duffy square; point = a + s (b - a) + s t (c - b)
-    def _integrate(self, chart, tx, tn, cells):
+    def _integrate(self, chart, tx, tn, cells, scale=None, offset=False):
         tgt, A, B, C, R = cells
         m = len(self.gx)
         s = R[:, 0:1] + (R[:, 1:2] - R[:, 0:1]) * self.gx[None, :]           # [nc, m]
@@ -129,25 +150,36 @@ class NearQuadrature:
         e1 = B - A
         e2 = C - B
         det = np.abs(e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
-        pu = A[:, 0:1] + S_ * e1[:, 0:1] + S_ * T_ * e2[:, 0:1]
-        pv = A[:, 1:2] + S_ * e1[:, 1:2] + S_ * T_ * e2[:, 1:2]
+        du = S_ * e1[:, 0:1] + S_ * T_ * e2[:, 0:1]
+        dv = S_ * e1[:, 1:2] + S_ * T_ * e2[:, 1:2]
         omega = (W_ * S_ * det[:, None]).ravel()
         nc = len(tgt)
-        y, ny, J, lag = chart.at(pu.ravel(), pv.ravel())
-        xt = np.repeat(tx[tgt], m * m, axis=0)
         nt = np.repeat(tn[tgt], m * m, axis=0)
-        K, r3 = kernel_values(xt, nt, y, ny)                                  # [P, 4]
+        if offset:
+            # self patch: every cell shares the apex a = the target's node
+            d, ny, J, lag = chart.at_offset(A[0, 0], A[0, 1], du.ravel(), dv.ravel())
+        else:
+            y, ny, J, lag = chart.at((A[:, 0:1] + du).ravel(), (A[:, 1:2] + dv).ravel())
+            d = np.repeat(tx[tgt], m * m, axis=0) - y
+        K, r3 = kernel_values_d(d, nt, ny)                                    # [P, 4]
         wJ = (omega * J).reshape(nc, m * m)
         f = np.einsum("cp,cpk,cpq->ckq", wJ, K.reshape(nc, m * m, 4),
                       lag.reshape(nc, m * m, -1), optimize=True)
-        rnd = (wJ * r3.reshape(nc, m * m)).sum(axis=1)
+        lmax = np.abs(lag).max(axis=1).reshape(nc, m * m)
+        if offset:
+            # d is accurate to eps |d|: numerators carry eps |d| r rounding
+            r2inv = (r3 * np.sqrt(np.sum(d * d, axis=1))).reshape(nc, m * m)
+            rnd = (wJ * r2inv * lmax).sum(axis=1)
+        else:
+            sc = 1.0 if scale is None else np.repeat(scale[tgt], 1)
+            rnd = (wJ * r3.reshape(nc, m * m) * lmax).sum(axis=1) * sc
         return f, rnd
 
-    def _integrate_chunked(self, chart, tx, tn, cells, chunk=1024):
+    def _integrate_chunked(self, chart, tx, tn, cells, scale=None, offset=False, chunk=1024):
         n = len(cells[0])
         outs, rnds = [], []
         for a in range(0, n, chunk):
-            o, r = self._integrate(chart, tx, tn, tuple(c[a:a + chunk] for c in cells))
+            o, r = self._integrate(chart, tx, tn, tuple(c[a:a + chunk] for c in cells), scale, offset)
             outs.append(o)
             rnds.append(r)
         return np.concatenate(outs), np.concatenate(rnds)
@@ -173,22 +205,24 @@ class NearQuadrature:
         return (np.repeat(tgt, 4), np.repeat(A, 4, axis=0), np.repeat(B, 4, axis=0),
                 np.repeat(C, 4, axis=0), np.stack(kids, 1).reshape(-1, 4))
 
-    def _adaptive(self, chart, tx, tn, roots, ntgt, tol, split, scale):
+    def _adaptive(self, chart, tx, tn, roots, ntgt, tol, split, scale, offset=False):
         out = np.zeros((ntgt, 4, self.geo.np_))
         cells = roots
-        est, _ = self._integrate_chunked(chart, tx, tn, cells)
+        est, _ = self._integrate_chunked(chart, tx, tn, cells, scale, offset)
         depth = 0
+        ncells = 0
         eps = np.finfo(np.float64).eps
         while len(cells[0]):
             kids = split(cells)
-            kid_est, kid_rnd = self._integrate_chunked(chart, tx, tn, kids)
+            kid_est, kid_rnd = self._integrate_chunked(chart, tx, tn, kids, scale, offset)
             nc = len(cells[0])
             ksum = kid_est.reshape(nc, 4, 4, -1).sum(axis=1)
-            floor = 16.0 * eps * scale[cells[0]] * kid_rnd.reshape(nc, 4).sum(axis=1)
+            floor = 64.0 * eps * kid_rnd.reshape(nc, 4).sum(axis=1)
             err = np.max(np.abs(ksum - est), axis=(1, 2))
             depth += 1
-            done = err <= np.maximum(tol, floor)
-            if depth >= self.max_depth:
+            done = (err <= np.maximum(tol, floor)) | (np.max(np.abs(ksum), axis=(1, 2)) <= tol)
+            ncells += 4 * nc
+            if depth >= self.max_depth or ncells > self.max_cells * ntgt:
                 self.depth_hits += int(np.count_nonzero(~done))
                 done[:] = True
             np.add.at(out, cells[0][done], ksum[done])
@@ -221,20 +255,13 @@ class NearQuadrature:
             res[idx] = self._adaptive(chart, tx[idx], tn[idx], roots, len(idx), tol,
                                       self._split_triangles, scale[idx])
         # self patch: three Duffy triangles with apex at the target's preimage
-        idx = np.nonzero(own)[0]
-        if len(idx):
-            apex = geo.basis.uv[targets[idx] % geo.np_]
-            verts = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
-            tg, A, B, C = [], [], [], []
-            for j in range(3):
-                tg.append(np.arange(len(idx)))
-                A.append(apex)
-                B.append(np.tile(verts[j], (len(idx), 1)))
-                C.append(np.tile(verts[(j + 1) % 3], (len(idx), 1)))
-            roots = (np.concatenate(tg), np.concatenate(A), np.concatenate(B), np.concatenate(C),
-                     np.tile([0.0, 1.0, 0.0, 1.0], (3 * len(idx), 1)))
-            res[idx] = self._adaptive(chart, tx[idx], tn[idx], roots, len(idx), tol,
-                                      self._split_rectangles, scale[idx])
+        verts = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+        for i in np.nonzero(own)[0]:
+            apex = geo.basis.uv[targets[i] % geo.np_]
+            roots = (np.zeros(3, dtype=np.int64), np.tile(apex, (3, 1)), verts[[0, 1, 2]], verts[[1, 2, 0]],
+                     np.tile([0.0, 1.0, 0.0, 1.0], (3, 1)))
+            res[i] = self._adaptive(chart, tx[[i]], tn[[i]], roots, 1, tol, self._split_rectangles,
+                                    scale[[i]], offset=True)[0]
         return res
 
 

@@ -1,0 +1,310 @@
+"""Python binding of the GB300 Laplace-Beltrami layer-potential library.
+
+Argument marshalling only: every computation runs in the CUDA library
+(_build/libgblb.so, built by build.py).  The names mirror the C ABI in
+include/gblb.h.  Arrays may be numpy arrays (host) or torch tensors (host or
+CUDA); they must be contiguous float64 (int64 / int32 for index arrays).
+Device tensors are passed by pointer; the library copies host arrays through
+its own device buffers.  Importing this package fails loudly when the shared
+library has not been built; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgblb.so")
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENOTCONVERGED, LB_ETIMEOUT, LB_EGEOM, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+LB_FP64, LB_FP32, LB_FP32_REFINED = 0, 1, 2
+LB_A2, LB_A3 = 2, 3
+LB_K_S, LB_K_D, LB_K_SP, LB_K_SPPDP = 0, 1, 2, 3
+NKERNELS = 4
+_STATUS = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOMEM", -3: "LB_ECUDA", -4: "LB_ENOTCONVERGED",
+           -5: "LB_ETIMEOUT", -6: "LB_EGEOM", -7: "LB_ESTATE"}
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [("eps_quad", ctypes.c_double), ("near_factor", ctypes.c_double),
+                ("precision", ctypes.c_int), ("formulation", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
+                ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int)]
+
+
+class lb_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("applies_fp64", ctypes.c_int32),
+                ("applies_fp32", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("removed_mean", ctypes.c_double),
+                ("history", ctypes.c_double * 128), ("history_len", ctypes.c_int32),
+                ("pairs", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "refinements": self.refinements,
+                "converged": bool(self.converged), "applies_fp64": self.applies_fp64,
+                "applies_fp32": self.applies_fp32, "nrhs": self.nrhs,
+                "rel_residual": self.rel_residual, "removed_mean": self.removed_mean,
+                "history": list(self.history[:self.history_len]), "pairs": self.pairs}
+
+
+class lb_geom_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("npatch", ctypes.c_int64), ("np", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("nnzb", ctypes.c_int64), ("area", ctypes.c_double),
+                ("sm_count", ctypes.c_int32), ("corrections", ctypes.c_int32)]
+
+
+PROF_NCAT = 16
+PROF_NAMES = {0: "far32_k1", 1: "far32_kall", 2: "far32_k2", 3: "far32_k4", 4: "far64_k1", 5: "far64_kall",
+              6: "far64_k2", 7: "far64_k4", 8: "epilogue_spmv", 9: "quad"}
+
+
+class lb_profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * PROF_NCAT), ("calls", ctypes.c_int64 * PROF_NCAT),
+                ("launches", ctypes.c_int64)]
+
+
+class LBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"CUDA library not built: {LIB_PATH} is missing; run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    sig = {
+        "lb_default_params": [P], "lb_create": [P, ctypes.c_int, P], "lb_destroy": [P],
+        "lb_set_params": [P, P], "lb_get_params": [P, P], "lb_set_stream": [P, P],
+        "lb_upload_geometry": [P, ctypes.c_int64, ctypes.c_int, P, P, P, P, P],
+        "lb_get_geometry": [P, P, P, P], "lb_geometry_info": [P, P], "lb_build_near": [P],
+        "lb_build_corrections": [P], "lb_load_corrections": [P, ctypes.c_int64, P, P, P],
+        "lb_get_corrections": [P, P, P, P], "lb_far_sums": [P, ctypes.c_int, ctypes.c_int, P, P],
+        "lb_apply_S": [P, ctypes.c_int, P, P], "lb_apply_Sp": [P, ctypes.c_int, P, P],
+        "lb_apply_D": [P, ctypes.c_int, P, P], "lb_apply_SppDp": [P, ctypes.c_int, P, P],
+        "lb_apply_gradS": [P, ctypes.c_int, P, P], "lb_apply_A": [P, ctypes.c_int, P, P],
+        "lb_solve_lb": [P, ctypes.c_int, P, P, P], "lb_harmonic_fields": [P, ctypes.c_int, P, P, P],
+        "lb_surface_div": [P, ctypes.c_int, P, P],
+        "lb_set_profiling": [P, ctypes.c_int], "lb_get_profile": [P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.lb_last_error.argtypes = [P]
+    lib.lb_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+lib = _lib
+
+
+def default_params(**kw) -> lb_params:
+    p = lb_params()
+    _lib.lb_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a, dtype):
+    """(pointer, keep-alive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            want = {np.float64: torch.float64, np.int64: torch.int64, np.int32: torch.int32}[dtype]
+            if a.dtype != want or not a.is_contiguous():
+                raise TypeError(f"tensor must be contiguous {want}")
+            return ctypes.c_void_p(a.data_ptr()), a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _out(a, dtype, shape):
+    if a is None:
+        arr = np.empty(shape, dtype=dtype)
+        return ctypes.c_void_p(arr.ctypes.data), arr
+    p, keep = _ptr(a, dtype)
+    if isinstance(keep, np.ndarray) and keep is not a:
+        raise TypeError("output array must be contiguous of the right dtype")
+    return p, keep
+
+
+class Context:
+    """One library context on one CUDA device (lb_create / lb_destroy)."""
+
+    def __init__(self, device: int = 0, params: lb_params | None = None, stream=None):
+        self._h = ctypes.c_void_p()
+        rc = _lib.lb_create(ctypes.byref(self._h), int(device),
+                            ctypes.byref(params) if params is not None else None)
+        if rc != LB_OK:
+            raise LBError(rc, _lib.lb_last_error(None).decode())
+        self.N = 0
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _check(self, rc, allow=()):
+        if rc != LB_OK and rc not in allow:
+            raise LBError(rc, _lib.lb_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if self._h:
+            _lib.lb_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- configuration -------------------------------------------------
+    def set_params(self, p: lb_params):
+        self._check(_lib.lb_set_params(self._h, ctypes.byref(p)))
+
+    def get_params(self) -> lb_params:
+        p = lb_params()
+        self._check(_lib.lb_get_params(self._h, ctypes.byref(p)))
+        return p
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None for the default."""
+        h = getattr(stream, "cuda_stream", stream)
+        self._check(_lib.lb_set_stream(self._h, ctypes.c_void_p(h or 0)))
+
+    def set_profiling(self, on: bool = True):
+        self._check(_lib.lb_set_profiling(self._h, 1 if on else 0))
+
+    def get_profile(self) -> dict:
+        p = lb_profile()
+        self._check(_lib.lb_get_profile(self._h, ctypes.byref(p)))
+        out = {"launches": p.launches}
+        for k, name in PROF_NAMES.items():
+            if p.calls[k]:
+                out[name] = {"ms": p.ms[k], "calls": p.calls[k]}
+        return out
+
+    # --- geometry ------------------------------------------------------
+    def upload_geometry(self, npatch, order, ref_uv, ref_w, X, Xu, Xv):
+        args = [_ptr(a, np.float64) for a in (ref_uv, ref_w, X, Xu, Xv)]
+        self._check(_lib.lb_upload_geometry(self._h, int(npatch), int(order), *[a[0] for a in args]))
+        self.N = self.info()["N"]
+
+    def upload_surface(self, surf):
+        """Convenience: upload a workloads.surfaces.Surface-like object."""
+        self.upload_geometry(surf.npatch, surf.order, surf.uv, surf.wref, surf.X, surf.Xu, surf.Xv)
+
+    def info(self) -> dict:
+        g = lb_geom_info()
+        self._check(_lib.lb_geometry_info(self._h, ctypes.byref(g)))
+        return {f: getattr(g, f) for f, _ in g._fields_}
+
+    def get_geometry(self):
+        N = self.N
+        n, w, H = np.empty((N, 3)), np.empty(N), np.empty(N)
+        self._check(_lib.lb_get_geometry(self._h, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(w.ctypes.data),
+                                         ctypes.c_void_p(H.ctypes.data)))
+        return n, w, H
+
+    def build_near(self):
+        self._check(_lib.lb_build_near(self._h))
+
+    def build_corrections(self):
+        return self._check(_lib.lb_build_corrections(self._h), allow=(LB_EGEOM,))
+
+    def load_corrections(self, row_ptr, patch, vals):
+        nnzb = int(np.asarray(patch).shape[0]) if not hasattr(patch, "shape") else int(patch.shape[0])
+        a = _ptr(row_ptr, np.int64)
+        b = _ptr(patch, np.int32)
+        c = _ptr(vals, np.float64)
+        self._check(_lib.lb_load_corrections(self._h, nnzb, a[0], b[0], c[0]))
+
+    def get_corrections(self, with_vals=True):
+        info = self.info()
+        N, nnzb, npn = info["N"], info["nnzb"], info["np"]
+        rp = np.empty(N + 1, dtype=np.int64)
+        pa = np.empty(nnzb, dtype=np.int32)
+        vals = np.empty((nnzb, NKERNELS, npn)) if with_vals else None
+        self._check(_lib.lb_get_corrections(self._h, ctypes.c_void_p(rp.ctypes.data),
+                                            ctypes.c_void_p(pa.ctypes.data),
+                                            ctypes.c_void_p(vals.ctypes.data) if with_vals else None))
+        return rp, pa, vals
+
+    # --- applies -------------------------------------------------------
+    def _nrhs(self, x, per=1):
+        n = int(np.prod(x.shape)) // (self.N * per)
+        if n * self.N * per != int(np.prod(x.shape)):
+            raise ValueError("array size is not a multiple of N")
+        return n
+
+    def far_sums(self, sigma, precision=LB_FP64, out=None):
+        nrhs = self._nrhs(sigma)
+        p, keep = _ptr(sigma, np.float64)
+        o, res = _out(out, np.float64, (nrhs, NKERNELS, self.N))
+        self._check(_lib.lb_far_sums(self._h, int(precision), nrhs, p, o))
+        return res
+
+    def _apply(self, fn, sigma, out, per_out=1):
+        nrhs = self._nrhs(sigma)
+        p, keep = _ptr(sigma, np.float64)
+        shape = (nrhs, self.N) if per_out == 1 else (nrhs, self.N, per_out)
+        o, res = _out(out, np.float64, shape)
+        self._check(fn(self._h, nrhs, p, o))
+        return res
+
+    def apply_S(self, sigma, out=None):
+        return self._apply(_lib.lb_apply_S, sigma, out)
+
+    def apply_Sp(self, sigma, out=None):
+        return self._apply(_lib.lb_apply_Sp, sigma, out)
+
+    def apply_D(self, sigma, out=None):
+        return self._apply(_lib.lb_apply_D, sigma, out)
+
+    def apply_SppDp(self, sigma, out=None):
+        return self._apply(_lib.lb_apply_SppDp, sigma, out)
+
+    def apply_gradS(self, sigma, out=None):
+        return self._apply(_lib.lb_apply_gradS, sigma, out, per_out=3)
+
+    def apply_A(self, tau, out=None):
+        return self._apply(_lib.lb_apply_A, tau, out)
+
+    def surface_div(self, F, out=None):
+        nrhs = self._nrhs(F, 3)
+        p, keep = _ptr(F, np.float64)
+        o, res = _out(out, np.float64, (nrhs, self.N))
+        self._check(_lib.lb_surface_div(self._h, nrhs, p, o))
+        return res
+
+    # --- solves --------------------------------------------------------
+    def solve_lb(self, f, out=None, allow_unconverged=False):
+        nrhs = self._nrhs(f)
+        p, keep = _ptr(f, np.float64)
+        o, res = _out(out, np.float64, (nrhs, self.N))
+        info = lb_solve_info()
+        self._check(_lib.lb_solve_lb(self._h, nrhs, p, o, ctypes.byref(info)),
+                    allow=(LB_ENOTCONVERGED,) if allow_unconverged else ())
+        return res, info.as_dict()
+
+    def harmonic_fields(self, F, out=None):
+        nF = self._nrhs(F, 3)
+        p, keep = _ptr(F, np.float64)
+        o, res = _out(out, np.float64, (2 * nF, self.N, 3))
+        info = lb_solve_info()
+        self._check(_lib.lb_harmonic_fields(self._h, nF, p, o, ctypes.byref(info)))
+        return res, info.as_dict()

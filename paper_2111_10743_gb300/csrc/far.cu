@@ -1,0 +1,639 @@
+// Far-field pair sums, near-field correction SpMV and the A2 / A3 applies.
+//
+// A discretised potential at node i (Section 4, the corrected Nystrom form)
+// is the smooth-rule sum over all sources outside Near(i) plus the sum of
+// precomputed correction blocks over the patches in Near(i):
+//   K[sigma]_i = sum_{j : patch(j) not in Near(i)} w_j K(x_i, x_j) sigma_j
+//              + sum_{P in Near(i)} sum_q W^K_{i,P}[q] sigma_{P,q}.
+// Kernels (Section 3), d = x - y, r = |d|, G = 1/(4 pi r):
+//   S = 1/(4 pi r),  D = n_y.d/(4 pi r^3),  S' = -n_x.d/(4 pi r^3),
+//   S''+D' = [3 (n_x.d)((n_x - n_y).d)/r^2 - |n_x - n_y|^2/2]/(4 pi r^3)
+// (for unit normals |n_x - n_y|^2/2 = 1 - n_x.n_y; the difference form avoids
+// cancellation in float32).
+//
+// Pair kernels (the FMM calls of Section 4.2 / 4.3, Table 1, done as exact
+// direct sums): each thread owns NT targets in registers, the CTA stages TS
+// sources at a time in shared memory (one float4/double4_32a of position and
+// charge, one of normal and second charge), and the source range is split
+// over gridDim.y so that every SM holds several CTAs; split partials are
+// reduced in a fixed order by the epilogue (deterministic).  Near pairs are
+// skipped exactly: a per-(target block, source tile) flag selects a masked
+// inner loop only where some target of the block has some patch of the tile
+// in its near list.  float32 sums accumulate per tile in float32 and are
+// folded into a float-float (TwoSum) running total after every tile.
+//
+// Operator applies (Sections 4.2, 4.3), W[f] = sum w f / sum w:
+//   A3: pass 1 (charge tau) -> mu1 = S' tau, mu2 = S tau;
+//       pass 2 (charges mu1, mu2; dipole for S''+D') ->
+//       A3 tau = -tau/4 + S'[mu1] - (S''+D')[mu2] - 2 H S'[mu2] + W S[mu2].
+//   A2: pass 1 (charge tau) -> S, D, S', S''+D' of tau;
+//       mu1 = D tau, mu2 = -(S''+D') tau - 2 H S' tau + W S tau;
+//       pass 2 -> A2 tau = -tau/4 + D[mu1] + S[mu2]
+//       (the printed "- D[mu1]" is read as + D[mu1]: A2 contains +D^2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+
+template <typename R> struct V4T;
+template <> struct V4T<float> { typedef float4 type; };
+template <> struct V4T<double> { typedef double4_32a type; };
+
+__device__ __forceinline__ float lb_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double lb_rsqrt(double x) { return rsqrt(x); }
+
+// float-float running total: hi + lo, updated with TwoSum (Knuth)
+struct FF {
+  float hi, lo;
+  __device__ __forceinline__ void add(float p) {
+    float s = hi + p;
+    float bp = s - hi;
+    float e = (hi - (s - bp)) + (p - bp);
+    hi = s;
+    lo += e;
+  }
+};
+
+template <int KIND> struct FarOut { static const int n = 4; };
+template <> struct FarOut<FAR_K4> { static const int n = 2; };
+
+template <typename R, int KIND>
+__device__ __forceinline__ void far_pair(const R tx, const R ty, const R tz, const R nx, const R ny, const R nz,
+                                         const typename V4T<R>::type& a, const typename V4T<R>::type& b,
+                                         bool masked, R* acc) {
+  const R dx = tx - a.x, dy = ty - a.y, dz = tz - a.z;
+  const R r2 = dx * dx + dy * dy + dz * dz;
+  R rinv = lb_rsqrt(r2);
+  if (masked) rinv = R(0);
+  if (KIND == FAR_K1) {
+    const R qr = a.w * rinv;
+    acc[0] += qr;
+    const R t = qr * rinv * rinv;
+    acc[1] += t * dx;
+    acc[2] += t * dy;
+    acc[3] += t * dz;
+  } else if (KIND == FAR_KALL) {
+    const R rinv2 = rinv * rinv;
+    const R rinv3 = rinv2 * rinv;
+    const R nxd = nx * dx + ny * dy + nz * dz;
+    const R nyd = b.x * dx + b.y * dy + b.z * dz;
+    const R ex = nx - b.x, ey = ny - b.y, ez = nz - b.z;
+    const R dnd = ex * dx + ey * dy + ez * dz;
+    const R dn2 = ex * ex + ey * ey + ez * ez;
+    const R qr3 = a.w * rinv3;
+    acc[0] += a.w * rinv;
+    acc[1] += qr3 * nyd;
+    acc[2] += qr3 * nxd;
+    acc[3] += qr3 * (R(3) * nxd * dnd * rinv2 - R(0.5) * dn2);
+  } else if (KIND == FAR_K2) {
+    const R rinv2 = rinv * rinv;
+    const R rinv3 = rinv2 * rinv;
+    const R nxd = nx * dx + ny * dy + nz * dz;
+    const R t = nxd * rinv3;
+    acc[0] += a.w * t;
+    acc[1] += b.w * rinv;
+    acc[2] += b.w * t;
+    const R ex = nx - b.x, ey = ny - b.y, ez = nz - b.z;
+    const R dnd = ex * dx + ey * dy + ez * dz;
+    const R dn2 = ex * ex + ey * ey + ez * ez;
+    acc[3] += b.w * rinv3 * (R(3) * nxd * dnd * rinv2 - R(0.5) * dn2);
+  } else {  // FAR_K4
+    const R rinv3 = rinv * rinv * rinv;
+    const R nyd = b.x * dx + b.y * dy + b.z * dz;
+    acc[0] += a.w * nyd * rinv3;
+    acc[1] += b.w * rinv;
+  }
+}
+
+template <typename R, int KIND, int NT, int NTH, int TS>
+__global__ void __launch_bounds__(NTH) k_far(int64_t N, int np, const typename V4T<R>::type* __restrict__ tpos,
+                                             const typename V4T<R>::type* __restrict__ tnrm,
+                                             const typename V4T<R>::type* __restrict__ srcA,
+                                             const typename V4T<R>::type* __restrict__ srcB,
+                                             const uint8_t* __restrict__ flags, int64_t ntiles,
+                                             const int64_t* __restrict__ row_ptr,
+                                             const int32_t* __restrict__ near_patch, int tiles_per_split,
+                                             double* __restrict__ part) {
+  typedef typename V4T<R>::type V4;
+  constexpr int NO = FarOut<KIND>::n;
+  constexpr bool kUseB = KIND != FAR_K1;
+  __shared__ V4 sA[TS];
+  __shared__ V4 sB[kUseB ? TS : 1];
+  __shared__ int sLp[TS];
+
+  const int64_t t0 = (int64_t)blockIdx.x * (NTH * NT);
+  R tx[NT], ty[NT], tz[NT], nx[NT], ny[NT], nz[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int64_t t = t0 + threadIdx.x + j * NTH;
+    const V4 p = tpos[t];
+    tx[j] = p.x; ty[j] = p.y; tz[j] = p.z;
+    if (KIND != FAR_K1 && KIND != FAR_K4) {
+      const V4 q = tnrm[t];
+      nx[j] = q.x; ny[j] = q.y; nz[j] = q.z;
+    } else {
+      nx[j] = ny[j] = nz[j] = R(0);
+    }
+  }
+  R acc[NT][NO];
+  FF tot[NT][NO];
+#pragma unroll
+  for (int j = 0; j < NT; ++j)
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      acc[j][o] = R(0);
+      tot[j][o].hi = 0.f;
+      tot[j][o].lo = 0.f;
+    }
+
+  const int64_t tile_b = (int64_t)blockIdx.y * tiles_per_split;
+  const int64_t tile_e = min(ntiles, tile_b + tiles_per_split);
+  for (int64_t tile = tile_b; tile < tile_e; ++tile) {
+    const int64_t s0 = tile * TS;
+    const int64_t P0 = s0 / np;
+    for (int s = threadIdx.x; s < TS; s += NTH) {
+      sA[s] = srcA[s0 + s];
+      if (kUseB) sB[s] = srcB[s0 + s];
+      sLp[s] = (int)((s0 + s) / np - P0);
+    }
+    __syncthreads();
+    const bool any_near = flags[(int64_t)blockIdx.x * ntiles + tile] != 0;
+    if (!any_near) {
+#pragma unroll 4
+      for (int s = 0; s < TS; ++s) {
+        const V4 a = sA[s];
+        const V4 b = kUseB ? sB[s] : a;
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+          far_pair<R, KIND>(tx[j], ty[j], tz[j], nx[j], ny[j], nz[j], a, b, false, acc[j]);
+      }
+    } else {
+      unsigned long long m[NT];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int64_t t = t0 + threadIdx.x + j * NTH;
+        m[j] = 0ull;
+        if (t < N)
+          for (int64_t bb = row_ptr[t]; bb < row_ptr[t + 1]; ++bb) {
+            const int64_t d = (int64_t)near_patch[bb] - P0;
+            if (d >= 0 && d < 64) m[j] |= 1ull << d;
+          }
+      }
+      for (int s = 0; s < TS; ++s) {
+        const V4 a = sA[s];
+        const V4 b = kUseB ? sB[s] : a;
+        const int lp = sLp[s];
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+          far_pair<R, KIND>(tx[j], ty[j], tz[j], nx[j], ny[j], nz[j], a, b, (m[j] >> lp) & 1ull, acc[j]);
+      }
+    }
+    if (sizeof(R) == 4) {
+#pragma unroll
+      for (int j = 0; j < NT; ++j)
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+          tot[j][o].add((float)acc[j][o]);
+          acc[j][o] = R(0);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int64_t t = t0 + threadIdx.x + j * NTH;
+    if (t >= N) continue;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      double v = (sizeof(R) == 4) ? (double)tot[j][o].hi + (double)tot[j][o].lo : (double)acc[j][o];
+      part[((int64_t)blockIdx.y * NO + o) * N + t] = v;
+    }
+  }
+}
+
+// flag (target block, source tile) pairs that contain a near pair
+__global__ void k_mask_flags(int64_t N, int np, int tb, int ts, int64_t ntiles, const int64_t* __restrict__ row_ptr,
+                             const int32_t* __restrict__ near_patch, uint8_t* __restrict__ flags) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t blk = i / tb;
+  for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+    const int64_t P = near_patch[b];
+    const int64_t f = (P * np) / ts, l = ((P + 1) * np - 1) / ts;
+    for (int64_t t = f; t <= l; ++t) flags[blk * ntiles + t] = 1;
+  }
+}
+
+static int get_mask(lb_ctx* c, int tb, int ts, MaskTable** out) {
+  for (auto& m : c->masks)
+    if (m.tb == tb && m.ts == ts) {
+      *out = &m;
+      return LB_OK;
+    }
+  MaskTable m;
+  m.tb = tb;
+  m.ts = ts;
+  m.ntb = (c->N + tb - 1) / tb;
+  m.ntiles = c->Npad / ts;
+  LB_CHECK(lb_alloc(c, &m.flags, (size_t)(m.ntb * m.ntiles)));
+  LB_CUDA(c, cudaMemsetAsync(m.flags, 0, (size_t)(m.ntb * m.ntiles), c->stream));
+  k_mask_flags<<<lb_div_up(c->N, 256), 256, 0, c->stream>>>(c->N, c->np, tb, ts, m.ntiles, c->row_ptr,
+                                                              c->near_patch, m.flags);
+  LB_LAUNCH(c);
+  c->masks.push_back(m);
+  *out = &c->masks.back();
+  return LB_OK;
+}
+
+template <typename R, int KIND, int NT, int NTH, int TS>
+static int launch_far_t(lb_ctx* c, const void* srcA, const void* srcB, double* part, int* nsplit_out) {
+  typedef typename V4T<R>::type V4;
+  const int tb = NT * NTH;
+  if (c->np * 62 < TS) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
+  MaskTable* m = nullptr;
+  LB_CHECK(get_mask(c, tb, TS, &m));
+  const int64_t ntb = m->ntb, ntiles = m->ntiles;
+  // enough CTAs for several per SM: split the source range
+  const int64_t want = 6LL * c->sm_count;
+  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(ntiles, (want + ntb - 1) / ntb));
+  const int tps = (int)((ntiles + nsplit - 1) / nsplit);
+  nsplit = (ntiles + tps - 1) / tps;
+  const V4* tp = sizeof(R) == 4 ? (const V4*)c->pos32 : (const V4*)c->pos64;
+  const V4* tn = sizeof(R) == 4 ? (const V4*)c->nrm32 : (const V4*)c->nrm64;
+  dim3 grid((unsigned)ntb, (unsigned)nsplit);
+  ProfScope prof(c, (sizeof(R) == 4 ? LB_PROF_FAR32_K1 : LB_PROF_FAR64_K1) + KIND);
+  k_far<R, KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, c->np, tp, tn, (const V4*)srcA, (const V4*)srcB,
+                                                          m->flags, ntiles, c->row_ptr, c->near_patch, tps, part);
+  LB_LAUNCH(c);
+  lb_pair_counter += c->N * c->N;
+  *nsplit_out = (int)nsplit;
+  return LB_OK;
+}
+
+int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* srcB, double* part, int* nsplit) {
+  if (prec == LB_FP64) {
+    switch (kind) {
+      case FAR_K1: return launch_far_t<double, FAR_K1, 2, 128, 64>(c, srcA, srcB, part, nsplit);
+      case FAR_KALL: return launch_far_t<double, FAR_KALL, 2, 128, 64>(c, srcA, srcB, part, nsplit);
+      case FAR_K2: return launch_far_t<double, FAR_K2, 2, 128, 64>(c, srcA, srcB, part, nsplit);
+      default: return launch_far_t<double, FAR_K4, 2, 128, 64>(c, srcA, srcB, part, nsplit);
+    }
+  }
+  switch (kind) {
+    case FAR_K1: return launch_far_t<float, FAR_K1, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+    case FAR_KALL: return launch_far_t<float, FAR_KALL, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+    case FAR_K2: return launch_far_t<float, FAR_K2, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+    default: return launch_far_t<float, FAR_K4, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// sources for a pass: A = (x, y, z, w * d1), B = (n, w * d2)
+template <typename R>
+__global__ void k_pack(int64_t N, int64_t Npad, const typename V4T<R>::type* __restrict__ pos,
+                       const typename V4T<R>::type* __restrict__ nrm, const double* __restrict__ w,
+                       const double* __restrict__ d1, const double* __restrict__ d2,
+                       typename V4T<R>::type* __restrict__ A, typename V4T<R>::type* __restrict__ B) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Npad) return;
+  typename V4T<R>::type p = pos[i], n = nrm[i];
+  if (i < N) {
+    p.w = (R)(w[i] * d1[i]);
+    n.w = d2 ? (R)(w[i] * d2[i]) : R(0);
+  } else {
+    p.w = R(0);
+    n.w = R(0);
+  }
+  A[i] = p;
+  B[i] = n;
+}
+
+static int pack_sources(lb_ctx* c, int prec, const double* d1, const double* d2, void** A, void** B) {
+  const size_t v4 = prec == LB_FP64 ? sizeof(double4_32a) : sizeof(float4);
+  LB_CHECK(lb_ensure(c, c->ws_src, 2 * c->Npad * v4));
+  *A = c->ws_src.p;
+  *B = (char*)c->ws_src.p + c->Npad * v4;
+  if (prec == LB_FP64)
+    k_pack<double><<<lb_div_up(c->Npad, 256), 256, 0, c->stream>>>(c->N, c->Npad, c->pos64, c->nrm64, c->w, d1, d2,
+                                                                    (double4_32a*)*A, (double4_32a*)*B);
+  else
+    k_pack<float><<<lb_div_up(c->Npad, 256), 256, 0, c->stream>>>(c->N, c->Npad, c->pos32, c->nrm32, c->w, d1, d2,
+                                                                   (float4*)*A, (float4*)*B);
+  LB_LAUNCH(c);
+  return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// epilogue: reduce split partials, add correction SpMV, one warp per row.
+struct EpiSpec {
+  int nout;
+  int acc[4];            // accumulator index, or -1 for -(n_x . (a1, a2, a3)) (K1's S')
+  double scale[4];       // multiplies the far accumulator
+  int kern[4];           // correction kernel (LB_K_*), or -1 for none
+  const double* dens[4]; // density of the correction sum
+  double* out[4];        // [N]
+};
+
+__global__ void k_epilogue(int64_t N, int np, int nsplit, int nacc, const double* __restrict__ part,
+                           const double* __restrict__ nrm, const int64_t* __restrict__ row_ptr,
+                           const int32_t* __restrict__ near_patch, const double* __restrict__ vals, EpiSpec sp) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (i >= N) return;
+  double cs[4] = {0, 0, 0, 0};
+  if (vals) {
+    const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
+    const int64_t ne = (re - rb) * np;
+    for (int64_t e = lane; e < ne; e += 32) {
+      const int64_t bo = e / np;
+      const int q = (int)(e - bo * np);
+      const int64_t b = rb + bo;
+      const int64_t col = (int64_t)near_patch[b] * np + q;
+      const double* vb = vals + b * (LB_NKERNELS * np) + q;
+#pragma unroll
+      for (int o = 0; o < 4; ++o)
+        if (o < sp.nout && sp.kern[o] >= 0) cs[o] = fma(vb[sp.kern[o] * np], sp.dens[o][col], cs[o]);
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) cs[o] += __shfl_xor_sync(0xffffffffu, cs[o], off);
+  }
+  if (lane != 0) return;
+  for (int o = 0; o < sp.nout; ++o) {
+    double f = 0;
+    if (sp.acc[o] >= 0) {
+      for (int s = 0; s < nsplit; ++s) f += part[((int64_t)s * nacc + sp.acc[o]) * N + i];
+    } else {
+      double g[3] = {0, 0, 0};
+      for (int s = 0; s < nsplit; ++s)
+        for (int k = 0; k < 3; ++k) g[k] += part[((int64_t)s * nacc + 1 + k) * N + i];
+      f = -(nrm[3 * i] * g[0] + nrm[3 * i + 1] * g[1] + nrm[3 * i + 2] * g[2]);
+    }
+    sp.out[o][i] = f * sp.scale[o] + cs[o];
+  }
+}
+
+static int run_epilogue(lb_ctx* c, int nsplit, int nacc, const double* part, const EpiSpec& sp) {
+  const int64_t threads = c->N * 32;
+  ProfScope prof(c, LB_PROF_EPILOGUE);
+  k_epilogue<<<lb_div_up(threads, 256), 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr,
+                                                             c->near_patch, c->have_corr ? c->vals : nullptr, sp);
+  LB_LAUNCH(c);
+  return LB_OK;
+}
+
+static int part_buffer(lb_ctx* c, double** part) {
+  // up to 4 accumulators x up to ntiles splits
+  const int64_t max_split = c->Npad / 64;
+  const int64_t want = std::min<int64_t>(max_split, 6LL * c->sm_count + 8);
+  LB_CHECK(lb_ensure(c, c->ws_part, (size_t)(want * 4 * c->N) * sizeof(double)));
+  *part = (double*)c->ws_part.p;
+  return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// deterministic weighted sums: partial per block, then a fixed-order total
+#define RED_BLOCKS 256
+__global__ void k_wdot_partial(int64_t N, const double* __restrict__ w, const double* __restrict__ v,
+                               double* __restrict__ partial) {
+  __shared__ double sh[256];
+  double s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    s += (w ? w[i] : 1.0) * v[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__device__ __forceinline__ double sum_partials(const double* p, int n) {
+  double s = 0;
+  for (int k = 0; k < n; ++k) s += p[k];
+  return s;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = sum_partials(partial, n);
+}
+
+int lb_wmean(lb_ctx* c, const double* f, double* mean_host) {
+  LB_CHECK(lb_ensure(c, c->ws_red, (RED_BLOCKS + 8) * sizeof(double)));
+  double* partial = (double*)c->ws_red.p;
+  k_wdot_partial<<<RED_BLOCKS, 256, 0, c->stream>>>(c->N, c->w, f, partial);
+  LB_LAUNCH(c);
+  k_sum_partials<<<1, 32, 0, c->stream>>>(partial, RED_BLOCKS, partial + RED_BLOCKS);
+  LB_LAUNCH(c);
+  LB_CUDA(c, cudaMemcpyAsync(c->host_pinned, partial + RED_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  *mean_host = c->host_pinned[0] / c->area;
+  return LB_OK;
+}
+
+// A3 final: out = -tau/4 + p0 - p3 - 2 H p2 + W p1  (p = S'mu1, S mu2, S'mu2, (S''+D')mu2)
+__global__ void k_a3_final(int64_t N, const double* __restrict__ tau, const double* __restrict__ pot,
+                           const double* __restrict__ H, const double* __restrict__ partial, int npart, double area,
+                           double* __restrict__ out) {
+  __shared__ double eta;
+  if (threadIdx.x == 0) eta = sum_partials(partial, npart) / area;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = -0.25 * tau[i] + pot[i] - pot[3 * N + i] - 2.0 * H[i] * pot[2 * N + i] + eta;
+}
+
+// A2 middle: mu1 = D tau (in place), mu2 = -(S''+D') tau - 2 H S' tau + W S tau
+__global__ void k_a2_mid(int64_t N, const double* __restrict__ pot, const double* __restrict__ H,
+                         const double* __restrict__ partial, int npart, double area, double* __restrict__ mu2) {
+  __shared__ double eta;
+  if (threadIdx.x == 0) eta = sum_partials(partial, npart) / area;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    mu2[i] = -pot[3 * N + i] - 2.0 * H[i] * pot[2 * N + i] + eta;
+}
+
+__global__ void k_a2_final(int64_t N, const double* __restrict__ tau, const double* __restrict__ q0,
+                           const double* __restrict__ q1, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = -0.25 * tau[i] + q0[i] + q1[i];
+}
+
+// ---------------------------------------------------------------------------
+int lb_potentials(lb_ctx* c, int prec, const double* sigma, double* pot, unsigned which) {
+  void *A, *B;
+  double* part;
+  int nsplit = 0;
+  LB_CHECK(part_buffer(c, &part));
+  const bool only_s = (which & ~((1u << LB_K_S) | (1u << LB_K_SP))) == 0;
+  LB_CHECK(pack_sources(c, prec, sigma, nullptr, &A, &B));
+  const int kind = only_s ? FAR_K1 : FAR_KALL;
+  LB_CHECK(lb_far_launch(c, kind, prec, A, B, part, &nsplit));
+  EpiSpec sp{};
+  int o = 0;
+  for (int k = 0; k < LB_NKERNELS; ++k) {
+    if (!(which & (1u << k))) continue;
+    if (kind == FAR_K1) {
+      sp.acc[o] = (k == LB_K_S) ? 0 : -1;
+      sp.scale[o] = LB_INV4PI;
+    } else {
+      sp.acc[o] = k;
+      sp.scale[o] = (k == LB_K_SP) ? -LB_INV4PI : LB_INV4PI;
+    }
+    sp.kern[o] = c->have_corr ? k : -1;
+    sp.dens[o] = sigma;
+    sp.out[o] = pot + (int64_t)k * c->N;
+    ++o;
+  }
+  sp.nout = o;
+  return run_epilogue(c, nsplit, 4, part, sp);
+}
+
+int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double* out) {
+  const int64_t N = c->N;
+  LB_CHECK(lb_ensure(c, c->ws_pot, (size_t)(8 * N) * sizeof(double)));
+  double* pot = (double*)c->ws_pot.p;   // [4][N] pass-1 potentials, then pass-2
+  double* mu = pot + 4 * N;             // mu1 [N], mu2 [N]
+  double* q = pot + 6 * N;              // pass-2 outputs (A2: 2 of them)
+  LB_CHECK(lb_ensure(c, c->ws_red, (RED_BLOCKS + 8) * sizeof(double)));
+  double* partial = (double*)c->ws_red.p;
+  double* part;
+  LB_CHECK(part_buffer(c, &part));
+  void *A, *B;
+  int nsplit = 0;
+  if (prec == LB_FP64) ++lb_apply64_counter; else ++lb_apply32_counter;
+  const unsigned nb = 4 * (unsigned)std::min<int64_t>(c->sm_count, lb_div_up(N, 256));
+  if (formulation == LB_A3) {
+    // pass 1: charge tau -> S tau, S' tau
+    LB_CHECK(pack_sources(c, prec, tau, nullptr, &A, &B));
+    LB_CHECK(lb_far_launch(c, FAR_K1, prec, A, B, part, &nsplit));
+    EpiSpec e1{};
+    e1.nout = 2;
+    e1.acc[0] = 0; e1.scale[0] = LB_INV4PI; e1.kern[0] = LB_K_S; e1.dens[0] = tau; e1.out[0] = mu + N;   // mu2
+    e1.acc[1] = -1; e1.scale[1] = LB_INV4PI; e1.kern[1] = LB_K_SP; e1.dens[1] = tau; e1.out[1] = mu;     // mu1
+    LB_CHECK(run_epilogue(c, nsplit, 4, part, e1));
+    // pass 2: charges mu1 (A.w), mu2 (B.w)
+    LB_CHECK(pack_sources(c, prec, mu, mu + N, &A, &B));
+    LB_CHECK(lb_far_launch(c, FAR_K2, prec, A, B, part, &nsplit));
+    EpiSpec e2{};
+    e2.nout = 4;
+    e2.acc[0] = 0; e2.scale[0] = -LB_INV4PI; e2.kern[0] = LB_K_SP; e2.dens[0] = mu; e2.out[0] = pot;
+    e2.acc[1] = 1; e2.scale[1] = LB_INV4PI; e2.kern[1] = LB_K_S; e2.dens[1] = mu + N; e2.out[1] = pot + N;
+    e2.acc[2] = 2; e2.scale[2] = -LB_INV4PI; e2.kern[2] = LB_K_SP; e2.dens[2] = mu + N; e2.out[2] = pot + 2 * N;
+    e2.acc[3] = 3; e2.scale[3] = LB_INV4PI; e2.kern[3] = LB_K_SPPDP; e2.dens[3] = mu + N; e2.out[3] = pot + 3 * N;
+    LB_CHECK(run_epilogue(c, nsplit, 4, part, e2));
+    k_wdot_partial<<<RED_BLOCKS, 256, 0, c->stream>>>(N, c->w, pot + N, partial);
+    LB_LAUNCH(c);
+    k_a3_final<<<nb, 256, 0, c->stream>>>(N, tau, pot, c->H, partial, RED_BLOCKS, c->area, out);
+    LB_LAUNCH(c);
+    return LB_OK;
+  }
+  // A2, pass 1: all four potentials of tau
+  LB_CHECK(pack_sources(c, prec, tau, nullptr, &A, &B));
+  LB_CHECK(lb_far_launch(c, FAR_KALL, prec, A, B, part, &nsplit));
+  EpiSpec e1{};
+  e1.nout = 4;
+  for (int k = 0; k < 4; ++k) {
+    e1.acc[k] = k;
+    e1.scale[k] = (k == LB_K_SP) ? -LB_INV4PI : LB_INV4PI;
+    e1.kern[k] = k;
+    e1.dens[k] = tau;
+    e1.out[k] = pot + (int64_t)k * N;
+  }
+  LB_CHECK(run_epilogue(c, nsplit, 4, part, e1));
+  k_wdot_partial<<<RED_BLOCKS, 256, 0, c->stream>>>(N, c->w, pot, partial);
+  LB_LAUNCH(c);
+  k_a2_mid<<<nb, 256, 0, c->stream>>>(N, pot, c->H, partial, RED_BLOCKS, c->area, mu + N);
+  LB_LAUNCH(c);
+  // pass 2: dipole mu1 = D tau (A.w), charge mu2 (B.w)
+  LB_CHECK(pack_sources(c, prec, pot + N, mu + N, &A, &B));
+  LB_CHECK(lb_far_launch(c, FAR_K4, prec, A, B, part, &nsplit));
+  EpiSpec e2{};
+  e2.nout = 2;
+  e2.acc[0] = 0; e2.scale[0] = LB_INV4PI; e2.kern[0] = LB_K_D; e2.dens[0] = pot + N; e2.out[0] = q;
+  e2.acc[1] = 1; e2.scale[1] = LB_INV4PI; e2.kern[1] = LB_K_S; e2.dens[1] = mu + N; e2.out[1] = q + N;
+  LB_CHECK(run_epilogue(c, nsplit, 2, part, e2));
+  k_a2_final<<<nb, 256, 0, c->stream>>>(N, tau, q, q + N, out);
+  LB_LAUNCH(c);
+  return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// public entry points
+static int pair_prec(lb_ctx* c) { return c->params.precision == LB_FP64 ? LB_FP64 : LB_FP32; }
+
+extern "C" int lb_far_sums(lb_ctx* c, int precision, int nrhs, const double* sigma, double* out) {
+  if (!c) return lb_fail(nullptr, LB_EINVAL, "null context");
+  if (!c->have_geom) return lb_fail(c, LB_ESTATE, "no geometry uploaded");
+  if (!c->have_near) LB_CHECK(lb_build_near(c));
+  if (nrhs < 1 || (precision != LB_FP64 && precision != LB_FP32)) return lb_fail(c, LB_EINVAL, "bad nrhs/precision");
+  LB_CUDA(c, cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  const double* din;
+  double* dout;
+  LB_CHECK(lb_stage_in(c, sigma, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
+  LB_CHECK(lb_stage_out(c, out, nrhs * 4 * N * sizeof(double), c->ws_stage_out, (void**)&dout));
+  double* part;
+  LB_CHECK(part_buffer(c, &part));
+  for (int r = 0; r < nrhs; ++r) {
+    void *A, *B;
+    int nsplit = 0;
+    LB_CHECK(pack_sources(c, precision, din + r * N, nullptr, &A, &B));
+    LB_CHECK(lb_far_launch(c, FAR_KALL, precision, A, B, part, &nsplit));
+    EpiSpec sp{};
+    sp.nout = 4;
+    for (int k = 0; k < 4; ++k) {
+      sp.acc[k] = k;
+      sp.scale[k] = (k == LB_K_SP) ? -LB_INV4PI : LB_INV4PI;
+      sp.kern[k] = -1;
+      sp.out[k] = dout + ((int64_t)r * 4 + k) * N;
+    }
+    k_epilogue<<<lb_div_up(N * 32, 256), 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr,
+                                                               c->near_patch, nullptr, sp);
+    LB_LAUNCH(c);
+  }
+  return lb_stage_out_finish(c, out, dout, nrhs * 4 * N * sizeof(double));
+}
+
+static int apply_kernel(lb_ctx* c, int k, int nrhs, const double* sigma, double* out) {
+  LB_CHECK(lb_require_corr(c));
+  if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
+  LB_CUDA(c, cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  const double* din;
+  double* dout;
+  LB_CHECK(lb_stage_in(c, sigma, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
+  LB_CHECK(lb_stage_out(c, out, nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dout));
+  LB_CHECK(lb_ensure(c, c->ws_vec, (size_t)(4 * N) * sizeof(double)));
+  double* pot = (double*)c->ws_vec.p;
+  for (int r = 0; r < nrhs; ++r) {
+    LB_CHECK(lb_potentials(c, pair_prec(c), din + r * N, pot, 1u << k));
+    LB_CUDA(c, cudaMemcpyAsync(dout + r * N, pot + (int64_t)k * N, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->stream));
+  }
+  return lb_stage_out_finish(c, out, dout, nrhs * N * sizeof(double));
+}
+
+extern "C" int lb_apply_S(lb_ctx* c, int nrhs, const double* s, double* o) { return apply_kernel(c, LB_K_S, nrhs, s, o); }
+extern "C" int lb_apply_Sp(lb_ctx* c, int nrhs, const double* s, double* o) { return apply_kernel(c, LB_K_SP, nrhs, s, o); }
+extern "C" int lb_apply_D(lb_ctx* c, int nrhs, const double* s, double* o) { return apply_kernel(c, LB_K_D, nrhs, s, o); }
+extern "C" int lb_apply_SppDp(lb_ctx* c, int nrhs, const double* s, double* o) {
+  return apply_kernel(c, LB_K_SPPDP, nrhs, s, o);
+}
+
+extern "C" int lb_apply_A(lb_ctx* c, int nrhs, const double* tau, double* out) {
+  LB_CHECK(lb_require_corr(c));
+  if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
+  LB_CUDA(c, cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  const double* din;
+  double* dout;
+  LB_CHECK(lb_stage_in(c, tau, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
+  LB_CHECK(lb_stage_out(c, out, nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dout));
+  for (int r = 0; r < nrhs; ++r)
+    LB_CHECK(lb_apply_op(c, c->params.formulation, pair_prec(c), din + r * N, dout + r * N));
+  return lb_stage_out_finish(c, out, dout, nrhs * N * sizeof(double));
+}

@@ -1,0 +1,175 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "gblb.h"
+
+#define LB_PI 3.14159265358979323846
+#define LB_INV4PI (1.0 / (4.0 * LB_PI))
+
+// Device buffer owned by a context; grows on demand and never shrinks.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Far-field kernel variants (which sums a pass accumulates).
+enum FarKind {
+  FAR_K1 = 0,    // charge q1: potential and gradient           -> S, grad S (S' = n.grad)
+  FAR_KALL = 1,  // charge q1: S, D, S', S''+D' of one density   (4 sums)
+  FAR_K2 = 2,    // A3 second pass: S'[mu1], S[mu2], S'[mu2], (S''+D')[mu2]
+  FAR_K4 = 3,    // A2 second pass: D[mu1], S[mu2]
+};
+
+// Cached tile-mask table for one (targets per block, sources per tile) shape.
+struct MaskTable {
+  int tb = 0, ts = 0;
+  int64_t ntb = 0, ntiles = 0;
+  uint8_t* flags = nullptr;  // [ntb][ntiles]: 1 when some pair in the block x tile is near
+};
+
+struct ProfPending {
+  int cat;
+  cudaEvent_t a, b;
+};
+
+struct lb_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  lb_params params{};
+  int sm_count = 0;
+  std::string err;
+
+  // geometry
+  bool have_geom = false;
+  int64_t N = 0, npatch = 0;
+  int np = 0, order = 0;
+  std::vector<double> ref_uv, ref_w;       // host copies of the node rule
+  std::vector<double> Vinv, Du, Dv;        // [np][np] host, row-major
+  double center[3] = {0, 0, 0};            // mean node position (float32 recentring)
+  double area = 0;
+
+  double* X = nullptr;     // [N][3]
+  double* Xu = nullptr;    // [N][3]
+  double* Xv = nullptr;    // [N][3]
+  double* nrm = nullptr;   // [N][3] unit normals from Xu x Xv
+  double* inrm = nullptr;  // [N][3] unit normals of the position interpolant
+  double* w = nullptr;     // [N]
+  double* H = nullptr;     // [N]
+  double* ginv = nullptr;  // [N][3]: g^11, g^12, g^22
+  double* J = nullptr;     // [N] |Xu x Xv|
+  double* cen = nullptr;   // [npatch][3]
+  double* rad = nullptr;   // [npatch]
+  double* area_p = nullptr;  // [npatch]
+  double* dVinv = nullptr;   // [np][np]
+  double* dDu = nullptr;     // [np][np]
+  double* dDv = nullptr;     // [np][np]
+  double* dref = nullptr;    // [np][3]: u, v, w of the node rule
+  float4* pos32 = nullptr;   // [Npad] (x-c, y-c, z-c, 0)
+  float4* nrm32 = nullptr;   // [Npad] (nx, ny, nz, 0)
+  double4_32a* pos64 = nullptr;  // [Npad] (x, y, z, 0)
+  double4_32a* nrm64 = nullptr;  // [Npad] (nx, ny, nz, 0)
+  int64_t Npad = 0;
+
+  // near lists and correction blocks
+  bool have_near = false, have_corr = false;
+  int64_t nnzb = 0;
+  int64_t* row_ptr = nullptr;   // [N+1]
+  int32_t* near_patch = nullptr;  // [nnzb]
+  double* vals = nullptr;       // [nnzb][4][np]
+  std::vector<MaskTable> masks;
+
+  // profiling
+  int prof_on = 0;
+  int64_t launches = 0;
+  std::vector<ProfPending> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[LB_PROF_NCAT] = {0};
+  int64_t prof_calls[LB_PROF_NCAT] = {0};
+
+  // workspace
+  DevBuf ws_part, ws_pot, ws_src, ws_vec, ws_red, ws_stage_in, ws_stage_out, ws_gm, ws_quad;
+  double* host_pinned = nullptr;  // small pinned scalars for GMRES control
+};
+
+// ---- error handling --------------------------------------------------------
+int lb_fail(lb_ctx* c, int code, const char* fmt, ...);
+#define LB_CUDA(c, expr)                                                              \
+  do {                                                                                \
+    cudaError_t e_ = (expr);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return lb_fail((c), LB_ECUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                     __FILE__, __LINE__);                                             \
+  } while (0)
+#define LB_CHECK(expr)       \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != LB_OK) return rc_; \
+  } while (0)
+#define LB_LAUNCH(c)   \
+  do {                 \
+    ++(c)->launches;   \
+    LB_CUDA(c, cudaGetLastError()); \
+  } while (0)
+
+// Times the launches enqueued during its lifetime under category `cat` when
+// profiling is on (two events recorded on the context stream).
+struct ProfScope {
+  lb_ctx* c;
+  int cat;
+  cudaEvent_t a = nullptr;
+  ProfScope(lb_ctx* ctx, int category);
+  ~ProfScope();
+};
+
+// ---- memory ----------------------------------------------------------------
+int lb_ensure(lb_ctx* c, DevBuf& b, size_t bytes);
+template <typename T>
+inline int lb_alloc(lb_ctx* c, T** p, size_t count) {
+  if (*p) { cudaFree(*p); *p = nullptr; }
+  if (count == 0) return LB_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) { *p = nullptr; return lb_fail(c, LB_ENOMEM, "cudaMalloc(%zu) failed: %s", count * sizeof(T), cudaGetErrorString(e)); }
+  return LB_OK;
+}
+template <typename T>
+inline void lb_free(T** p) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+}
+
+// Host-or-device argument staging: returns a device pointer holding `bytes`
+// of the caller's data (the caller's own pointer when it is device memory).
+int lb_stage_in(lb_ctx* c, const void* src, size_t bytes, DevBuf& tmp, const void** dev);
+// For outputs: returns a device pointer to write; lb_stage_out_finish copies
+// it back to the caller when the caller passed host memory.
+int lb_is_device_ptr(const void* p);
+int lb_stage_out(lb_ctx* c, void* dst, size_t bytes, DevBuf& tmp, void** dev);
+int lb_stage_out_finish(lb_ctx* c, void* dst, const void* dev, size_t bytes);
+
+// ---- host numerics (node rule matrices) ------------------------------------
+int lb_host_basis_matrices(lb_ctx* c);  // fills Vinv, Du, Dv from ref_uv
+
+// ---- internals used across files -------------------------------------------
+int lb_require_corr(lb_ctx* c);
+int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* srcB,
+                  double* part, int* nsplit_out);
+// potentials of one density: far + near, writes pot[k][N] for k in `which` bitmask
+// (bit K set -> pot + K*N holds K[sigma]); density on device, float64
+int lb_potentials(lb_ctx* c, int prec, const double* sigma, double* pot, unsigned which);
+// apply the formulation operator to one vector (device in, device out)
+int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double* out);
+// weighted mean of a device vector (deterministic), result to host
+int lb_wmean(lb_ctx* c, const double* f, double* mean_host);
+// counters of the last solve
+extern thread_local int64_t lb_pair_counter;
+extern thread_local int lb_apply64_counter, lb_apply32_counter;
+
+static inline unsigned lb_div_up(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }

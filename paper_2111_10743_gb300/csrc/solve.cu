@@ -1,0 +1,587 @@
+// GMRES, the mean-zero Laplace-Beltrami solve, mixed-precision refinement,
+// surface differential operators and harmonic vector fields.
+//
+// GMRES (Section 6: relative residual below tol, at most max_iter = 100
+// iterations): x0 = 0, no restart, Euclidean inner product.  The Arnoldi
+// basis lives on the device in float64; orthogonalisation is classical
+// Gram-Schmidt applied twice (CGS2), whose two passes are each one multi-dot
+// and one multi-axpy over all previous vectors; the Hessenberg column, the
+// Givens rotations and the residual estimate |g_{j+1}| / |b| are updated by
+// a single-thread kernel, and only that scalar is read back per iteration.
+// Reductions are fixed-order (per-block partials, then an ordered sum).
+//
+// Mixed precision (LB_FP32_REFINED): float32 pair sums are accurate to about
+// 1e-6, so an inner GMRES on the float32 operator to inner_tol is wrapped in
+// iterative refinement whose residual b - A x uses float64 pair sums.
+//
+// Surface operators (Section 2), by nodal differentiation within a patch:
+//   grad_Gamma f = (g^11 f_u + g^12 f_v) X_u + (g^21 f_u + g^22 f_v) X_v,
+//   div_Gamma F = |X_u x X_v|^-1 (d_u(|X_u x X_v| F^1) + d_v(|X_u x X_v| F^2)),
+//   F^a = g^ab (F . X_b).
+// Harmonic fields (Section 5): Delta alpha = div F, Delta beta =
+// -div(n x F), H = F - grad alpha - n x grad beta, and n x H.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+#define GM_RB 128  // reduction blocks of the multi-dot
+
+__global__ void k_multidot(int64_t N, int nvec, const double* __restrict__ V, int64_t ldv,
+                           const double* __restrict__ w, double* __restrict__ partial) {
+  __shared__ double sh[256];
+  for (int v = 0; v < nvec; ++v) {
+    const double* Vv = V + (int64_t)v * ldv;
+    double s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+      s += Vv[i] * w[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+      if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)v * gridDim.x + blockIdx.x] = sh[0];
+    __syncthreads();
+  }
+}
+
+// out[v] (+)= ordered sum of the partials of vector v
+__global__ void k_reduce_cols(int nvec, int nblk, const double* __restrict__ partial, double* __restrict__ out,
+                              int accumulate) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvec) return;
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)v * nblk + b];
+  out[v] = accumulate ? out[v] + s : s;
+}
+
+// w -= sum_v h[v] V[v]
+__global__ void k_axpy_multi(int64_t N, int nvec, const double* __restrict__ V, int64_t ldv,
+                             const double* __restrict__ h, double* __restrict__ w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int v = 0; v < nvec; ++v) s -= h[v] * V[(int64_t)v * ldv + i];
+    w[i] = s;
+  }
+}
+
+// y = x / *s  (s on the device; zero output when *s == 0); y may equal x
+__global__ void k_scale_by(int64_t N, const double* __restrict__ x, const double* __restrict__ s, double* y) {
+  const double d = s[0] != 0.0 ? 1.0 / s[0] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * d;
+}
+
+__global__ void k_add_small(int n, const double* __restrict__ a, double* __restrict__ b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] += a[i];
+}
+
+// x = sum_v y[v] V[v]  (+ x when accumulate)
+__global__ void k_combine(int64_t N, int nvec, const double* __restrict__ V, int64_t ldv,
+                          const double* __restrict__ y, double* __restrict__ x, int accumulate) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = accumulate ? x[i] : 0.0;
+    for (int v = 0; v < nvec; ++v) s += y[v] * V[(int64_t)v * ldv + i];
+    x[i] = s;
+  }
+}
+
+__global__ void k_sqrt_to(const double* __restrict__ a, double* __restrict__ b) {
+  if (threadIdx.x == 0) b[0] = sqrt(a[0]);
+}
+
+// Hessenberg column j (h[0..j], hn = h[j+1]) -> rotations, g, residual
+__global__ void k_givens(int j, int ldh, const double* __restrict__ h, double* __restrict__ Hm,
+                         double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g, double beta,
+                         double* __restrict__ resid) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* col = Hm + (int64_t)j * ldh;
+  for (int i = 0; i <= j + 1; ++i) col[i] = h[i];
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double r = hypot(a, b);
+  const double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+  cs[j] = c;
+  sn[j] = s;
+  col[j] = r;
+  col[j + 1] = 0.0;
+  g[j + 1] = -s * g[j];
+  g[j] = c * g[j];
+  resid[0] = fabs(g[j + 1]) / beta;
+  resid[1] = r;
+}
+
+__global__ void k_backsolve(int k, int ldh, const double* __restrict__ Hm, const double* __restrict__ g,
+                            double* __restrict__ y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int l = i + 1; l < k; ++l) s -= Hm[(int64_t)l * ldh + i] * y[l];
+    const double d = Hm[(int64_t)i * ldh + i];
+    y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+__global__ void k_sub_scalar(int64_t N, const double* __restrict__ x, double m, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] - m;
+}
+
+__global__ void k_axpby(int64_t N, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_check_finite(int64_t N, const double* __restrict__ x, int* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) atomicExch(bad, 1);
+}
+
+// ---------------------------------------------------------------------------
+struct Gm {
+  int m, ldh;
+  double *V, *h, *Hm, *cs, *sn, *g, *y, *partial, *scal, *w;
+};
+
+static int gm_work(lb_ctx* c, int m, Gm* G) {
+  const int64_t N = c->N;
+  const int ldh = m + 1;
+  size_t need = (size_t)(m + 1) * N + (size_t)(m + 2) + (size_t)ldh * m + 3 * (size_t)(m + 2) + (size_t)(m + 2) +
+                (size_t)GM_RB * (m + 2) + 8 + N;
+  LB_CHECK(lb_ensure(c, c->ws_gm, need * sizeof(double)));
+  double* p = (double*)c->ws_gm.p;
+  G->m = m;
+  G->ldh = ldh;
+  G->V = p; p += (size_t)(m + 1) * N;
+  G->h = p; p += m + 2;
+  G->Hm = p; p += (size_t)ldh * m;
+  G->cs = p; p += m + 2;
+  G->sn = p; p += m + 2;
+  G->g = p; p += m + 2;
+  G->y = p; p += m + 2;
+  G->partial = p; p += (size_t)GM_RB * (m + 2);
+  G->scal = p; p += 8;
+  G->w = p;
+  return LB_OK;
+}
+
+static unsigned vec_blocks(lb_ctx* c) { return (unsigned)std::min<int64_t>(4 * c->sm_count, lb_div_up(c->N, 256)); }
+
+// squared norm / dots into dst (device) via fixed-order partials
+static int dots(lb_ctx* c, Gm& G, int nvec, const double* V, const double* w, double* dst, int accumulate) {
+  k_multidot<<<GM_RB, 256, 0, c->stream>>>(c->N, nvec, V, c->N, w, G.partial);
+  LB_LAUNCH(c);
+  k_reduce_cols<<<lb_div_up(nvec, 64), 64, 0, c->stream>>>(nvec, GM_RB, G.partial, dst, accumulate);
+  LB_LAUNCH(c);
+  return LB_OK;
+}
+
+static int read_scalar(lb_ctx* c, const double* d, double* h) {
+  LB_CUDA(c, cudaMemcpyAsync(c->host_pinned, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  *h = c->host_pinned[0];
+  return LB_OK;
+}
+
+// GMRES on the formulation operator with pair precision prec.
+// x (device) receives the solution; *iters the iteration count, *res the
+// final residual estimate; hist (may be null) the estimates per iteration.
+static int gmres(lb_ctx* c, int prec, const double* b, double* x, double tol, int max_iter, int* iters, double* res,
+                 std::vector<double>* hist) {
+  const int64_t N = c->N;
+  Gm G;
+  LB_CHECK(gm_work(c, max_iter, &G));
+  const unsigned nb = vec_blocks(c);
+  double beta2 = 0;
+  LB_CHECK(dots(c, G, 1, b, b, G.scal + 2, 0));
+  LB_CHECK(read_scalar(c, G.scal + 2, &beta2));
+  const double beta = sqrt(beta2);
+  *iters = 0;
+  *res = 0;
+  if (!std::isfinite(beta)) return lb_fail(c, LB_EINVAL, "non-finite right-hand side");
+  if (!(beta > 0)) {
+    LB_CUDA(c, cudaMemsetAsync(x, 0, N * sizeof(double), c->stream));
+    return LB_OK;
+  }
+  LB_CUDA(c, cudaMemsetAsync(G.g, 0, (G.m + 2) * sizeof(double), c->stream));
+  c->host_pinned[8] = beta;
+  LB_CUDA(c, cudaMemcpyAsync(G.g, c->host_pinned + 8, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  k_sqrt_to<<<1, 32, 0, c->stream>>>(G.scal + 2, G.scal + 3);
+  LB_LAUNCH(c);
+  k_scale_by<<<nb, 256, 0, c->stream>>>(N, b, G.scal + 3, G.V);
+  LB_LAUNCH(c);
+  if (hist) hist->push_back(1.0);
+  int k = 0;
+  double r = 1.0;
+  for (int j = 0; j < max_iter; ++j) {
+    const double* vj = G.V + (int64_t)j * N;
+    double* vn = G.V + (int64_t)(j + 1) * N;
+    LB_CHECK(lb_apply_op(c, c->params.formulation, prec, vj, G.w));
+    // classical Gram-Schmidt, twice: h = V^T w, w -= V h, h2 = V^T w, w -= V h2, h += h2
+    LB_CHECK(dots(c, G, j + 1, G.V, G.w, G.h, 0));
+    k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, j + 1, G.V, N, G.h, G.w);
+    LB_LAUNCH(c);
+    LB_CHECK(dots(c, G, j + 1, G.V, G.w, G.y, 0));
+    k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, j + 1, G.V, N, G.y, G.w);
+    LB_LAUNCH(c);
+    k_add_small<<<lb_div_up(j + 1, 128), 128, 0, c->stream>>>(j + 1, G.y, G.h);
+    LB_LAUNCH(c);
+    LB_CHECK(dots(c, G, 1, G.w, G.w, G.scal + 2, 0));
+    k_sqrt_to<<<1, 32, 0, c->stream>>>(G.scal + 2, G.h + j + 1);
+    LB_LAUNCH(c);
+    k_scale_by<<<nb, 256, 0, c->stream>>>(N, G.w, G.h + j + 1, vn);
+    LB_LAUNCH(c);
+    k_givens<<<1, 32, 0, c->stream>>>(j, G.ldh, G.h, G.Hm, G.cs, G.sn, G.g, beta, G.scal);
+    LB_LAUNCH(c);
+    LB_CHECK(read_scalar(c, G.scal, &r));
+    if (hist) hist->push_back(r);
+    k = j + 1;
+    if (!std::isfinite(r)) return lb_fail(c, LB_EINVAL, "GMRES breakdown: non-finite residual");
+    if (r < tol || r == 0.0) break;
+  }
+  k_backsolve<<<1, 32, 0, c->stream>>>(k, G.ldh, G.Hm, G.g, G.y);
+  LB_LAUNCH(c);
+  k_combine<<<nb, 256, 0, c->stream>>>(N, k, G.V, N, G.y, x, 0);
+  LB_LAUNCH(c);
+  *iters = k;
+  *res = r;
+  return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// norms and mean projection helpers on the context stream
+static int norm2(lb_ctx* c, const double* v, double* out) {
+  Gm G;
+  LB_CHECK(gm_work(c, 1, &G));
+  LB_CHECK(dots(c, G, 1, v, v, G.scal + 2, 0));
+  double s = 0;
+  LB_CHECK(read_scalar(c, G.scal + 2, &s));
+  *out = sqrt(s);
+  return LB_OK;
+}
+
+static int project_mean_zero(lb_ctx* c, const double* f, double* out, double* removed) {
+  double m = 0;
+  LB_CHECK(lb_wmean(c, f, &m));
+  k_sub_scalar<<<vec_blocks(c), 256, 0, c->stream>>>(c->N, f, m, out);
+  LB_LAUNCH(c);
+  if (removed) *removed = m;
+  return LB_OK;
+}
+
+// S applied with precision prec (far + near), device in/out
+static int apply_S_dev(lb_ctx* c, int prec, const double* s, double* out) {
+  LB_CHECK(lb_ensure(c, c->ws_vec, (size_t)(4 * c->N) * sizeof(double)));
+  double* pot = (double*)c->ws_vec.p;
+  LB_CHECK(lb_potentials(c, prec, s, pot, 1u << LB_K_S));
+  LB_CUDA(c, cudaMemcpyAsync(out, pot, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return LB_OK;
+}
+
+// one right-hand side: b (device) -> sigma (device)
+static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch, lb_solve_info* info, int first) {
+  const int64_t N = c->N;
+  const lb_params& p = c->params;
+  std::vector<double> hist;
+  int it = 0;
+  double res = 0;
+  const unsigned nb = vec_blocks(c);
+  if (p.precision != LB_FP32_REFINED) {
+    LB_CHECK(gmres(c, p.precision, b, sigma, p.tol, p.max_iter, &it, &res, first ? &hist : nullptr));
+    if (info) {
+      info->iterations += it;
+      info->converged = info->converged && (res < p.tol);
+      info->rel_residual = std::max(info->rel_residual, res);
+    }
+  } else {
+    // iterative refinement: sigma = 0, r = b; repeat  delta = GMRES32(r); sigma += delta; r = b - A64 sigma
+    double* r = scratch;
+    double* delta = scratch + N;
+    double* Ax = scratch + 2 * N;
+    double nbv = 0, rn = 0;
+    LB_CHECK(norm2(c, b, &nbv));
+    LB_CUDA(c, cudaMemsetAsync(sigma, 0, N * sizeof(double), c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    bool ok = nbv == 0.0;
+    int steps = 0;
+    double rel = nbv == 0.0 ? 0.0 : 1.0;
+    if (first) hist.push_back(1.0);
+    for (int s = 0; s < p.max_refine && !ok; ++s) {
+      int its = 0;
+      double ires = 0;
+      LB_CHECK(gmres(c, LB_FP32, r, delta, p.inner_tol, p.max_iter, &its, &ires, nullptr));
+      it += its;
+      k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, delta, 1.0, sigma);
+      LB_LAUNCH(c);
+      LB_CHECK(lb_apply_op(c, p.formulation, LB_FP64, sigma, Ax));
+      LB_CUDA(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, Ax, 1.0, r);
+      LB_LAUNCH(c);
+      LB_CHECK(norm2(c, r, &rn));
+      rel = rn / nbv;
+      ++steps;
+      if (first) hist.push_back(rel);
+      if (rel < p.tol) ok = true;
+    }
+    res = rel;
+    if (info) {
+      info->iterations += it;
+      info->refinements += steps;
+      info->converged = info->converged && ok;
+      info->rel_residual = std::max(info->rel_residual, rel);
+    }
+  }
+  if (info && first) {
+    info->history_len = (int32_t)std::min<size_t>(hist.size(), 128);
+    for (int i = 0; i < info->history_len; ++i) info->history[i] = hist[i];
+  }
+  return LB_OK;
+}
+
+static int solve_batch(lb_ctx* c, int nrhs, const double* f, double* u, lb_solve_info* info) {
+  const int64_t N = c->N;
+  const lb_params& p = c->params;
+  LB_CHECK(lb_ensure(c, c->ws_quad, (size_t)(6 * N) * sizeof(double)));
+  double* fb = (double*)c->ws_quad.p;    // projected f, then b
+  double* sig = fb + N;
+  double* scratch = fb + 2 * N;          // 3 N for refinement
+  double* tmp = fb + 5 * N;
+  // solution potentials: float32 pairs only in the plain float32 mode
+  const int post = p.precision == LB_FP32 ? LB_FP32 : LB_FP64;
+  int* dbad = nullptr;
+  LB_CHECK(lb_ensure(c, c->ws_red, 4096));
+  dbad = (int*)((char*)c->ws_red.p + 3072);
+  for (int r = 0; r < nrhs; ++r) {
+    const double* fr = f + (int64_t)r * N;
+    LB_CUDA(c, cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
+    k_check_finite<<<vec_blocks(c), 256, 0, c->stream>>>(N, fr, dbad);
+    LB_LAUNCH(c);
+    int bad = 0;
+    LB_CUDA(c, cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad) return lb_fail(c, LB_EINVAL, "right-hand side %d has non-finite entries", r);
+    double removed = 0;
+    LB_CHECK(project_mean_zero(c, fr, fb, &removed));
+    if (info && r == 0) info->removed_mean = removed;
+    if (p.formulation == LB_A2) {  // b = S[f]
+      LB_CHECK(apply_S_dev(c, post, fb, tmp));
+      LB_CUDA(c, cudaMemcpyAsync(fb, tmp, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    LB_CHECK(solve_one(c, fb, sig, scratch, info, r == 0));
+    double* ur = u + (int64_t)r * N;
+    if (p.formulation == LB_A3) {  // u = S[S[sigma]]
+      LB_CHECK(apply_S_dev(c, post, sig, tmp));
+      LB_CHECK(apply_S_dev(c, post, tmp, ur));
+    } else {
+      LB_CHECK(apply_S_dev(c, post, sig, ur));
+    }
+  }
+  return LB_OK;
+}
+
+extern "C" int lb_solve_lb(lb_ctx* c, int nrhs, const double* f, double* u, lb_solve_info* info) {
+  LB_CHECK(lb_require_corr(c));
+  if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
+  LB_CUDA(c, cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  if (info) {
+    *info = lb_solve_info{};
+    info->converged = 1;
+    info->nrhs = nrhs;
+  }
+  lb_pair_counter = 0;
+  lb_apply64_counter = lb_apply32_counter = 0;
+  const double* din;
+  double* dout;
+  LB_CHECK(lb_stage_in(c, f, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
+  LB_CHECK(lb_stage_out(c, u, nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dout));
+  LB_CHECK(solve_batch(c, nrhs, din, dout, info));
+  LB_CHECK(lb_stage_out_finish(c, u, dout, nrhs * N * sizeof(double)));
+  if (info) {
+    info->pairs = lb_pair_counter;
+    info->applies_fp64 = lb_apply64_counter;
+    info->applies_fp32 = lb_apply32_counter;
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!info->converged) return lb_fail(c, LB_ENOTCONVERGED, "GMRES did not reach tol %.3g (residual %.3g)",
+                                         c->params.tol, info->rel_residual);
+  }
+  return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// surface gradient and divergence by nodal differentiation (Section 2)
+
+__global__ void k_surf_grad(int64_t N, int np, const double* __restrict__ f, const double* __restrict__ Du,
+                            const double* __restrict__ Dv, const double* __restrict__ ginv,
+                            const double* __restrict__ Xu, const double* __restrict__ Xv,
+                            const double* __restrict__ add_n, const double* __restrict__ nrm,
+                            double* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t P = i / np;
+  const int q = (int)(i - P * np);
+  double fu = 0, fv = 0;
+  for (int b = 0; b < np; ++b) {
+    const double x = f[P * np + b];
+    fu += Du[q * np + b] * x;
+    fv += Dv[q * np + b] * x;
+  }
+  const double a = ginv[3 * i] * fu + ginv[3 * i + 1] * fv;
+  const double bb = ginv[3 * i + 1] * fu + ginv[3 * i + 2] * fv;
+  for (int k = 0; k < 3; ++k) {
+    double g = a * Xu[3 * i + k] + bb * Xv[3 * i + k];
+    if (add_n) g += add_n[i] * nrm[3 * i + k];
+    out[3 * i + k] = g;
+  }
+}
+
+// P1 = J F^1, P2 = J F^2 with F^a = g^ab (F . X_b); cross_n: use n x F instead of F
+__global__ void k_div_prep(int64_t N, const double* __restrict__ F, int cross_n, const double* __restrict__ nrm,
+                           const double* __restrict__ ginv, const double* __restrict__ Xu,
+                           const double* __restrict__ Xv, const double* __restrict__ J, double* __restrict__ P) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double v[3] = {F[3 * i], F[3 * i + 1], F[3 * i + 2]};
+  if (cross_n) {
+    const double* n = nrm + 3 * i;
+    const double c0 = n[1] * v[2] - n[2] * v[1], c1 = n[2] * v[0] - n[0] * v[2], c2 = n[0] * v[1] - n[1] * v[0];
+    v[0] = c0; v[1] = c1; v[2] = c2;
+  }
+  const double a = v[0] * Xu[3 * i] + v[1] * Xu[3 * i + 1] + v[2] * Xu[3 * i + 2];
+  const double b = v[0] * Xv[3 * i] + v[1] * Xv[3 * i + 1] + v[2] * Xv[3 * i + 2];
+  P[i] = J[i] * (ginv[3 * i] * a + ginv[3 * i + 1] * b);
+  P[N + i] = J[i] * (ginv[3 * i + 1] * a + ginv[3 * i + 2] * b);
+}
+
+__global__ void k_div_finish(int64_t N, int np, const double* __restrict__ P, const double* __restrict__ Du,
+                             const double* __restrict__ Dv, const double* __restrict__ J, double scale,
+                             double* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t p = i / np;
+  const int q = (int)(i - p * np);
+  double s = 0;
+  for (int b = 0; b < np; ++b) s += Du[q * np + b] * P[p * np + b] + Dv[q * np + b] * P[N + p * np + b];
+  out[i] = scale * s / J[i];
+}
+
+static int surface_div_dev(lb_ctx* c, const double* F, int cross_n, double scale, double* out) {
+  LB_CHECK(lb_ensure(c, c->ws_vec, (size_t)(4 * c->N) * sizeof(double)));
+  double* P = (double*)c->ws_vec.p;
+  k_div_prep<<<lb_div_up(c->N, 128), 128, 0, c->stream>>>(c->N, F, cross_n, c->nrm, c->ginv, c->Xu, c->Xv, c->J, P);
+  LB_LAUNCH(c);
+  k_div_finish<<<lb_div_up(c->N, 128), 128, 0, c->stream>>>(c->N, c->np, P, c->dDu, c->dDv, c->J, scale, out);
+  LB_LAUNCH(c);
+  return LB_OK;
+}
+
+extern "C" int lb_surface_div(lb_ctx* c, int nrhs, const double* F, double* out) {
+  if (!c) return lb_fail(nullptr, LB_EINVAL, "null context");
+  if (!c->have_geom) return lb_fail(c, LB_ESTATE, "no geometry uploaded");
+  if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
+  LB_CUDA(c, cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  const double* din;
+  double* dout;
+  LB_CHECK(lb_stage_in(c, F, nrhs * 3 * N * sizeof(double), c->ws_stage_in, (const void**)&din));
+  LB_CHECK(lb_stage_out(c, out, nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dout));
+  for (int r = 0; r < nrhs; ++r) LB_CHECK(surface_div_dev(c, din + (int64_t)r * 3 * N, 0, 1.0, dout + r * N));
+  return lb_stage_out_finish(c, out, dout, nrhs * N * sizeof(double));
+}
+
+extern "C" int lb_apply_gradS(lb_ctx* c, int nrhs, const double* sigma, double* out) {
+  LB_CHECK(lb_require_corr(c));
+  if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
+  LB_CUDA(c, cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  const double* din;
+  double* dout;
+  LB_CHECK(lb_stage_in(c, sigma, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
+  LB_CHECK(lb_stage_out(c, out, nrhs * 3 * N * sizeof(double), c->ws_stage_out, (void**)&dout));
+  LB_CHECK(lb_ensure(c, c->ws_quad, (size_t)(4 * N) * sizeof(double)));
+  double* pot = (double*)c->ws_quad.p;
+  const int prec = c->params.precision == LB_FP64 ? LB_FP64 : LB_FP32;
+  for (int r = 0; r < nrhs; ++r) {
+    LB_CHECK(lb_potentials(c, prec, din + r * N, pot, (1u << LB_K_S) | (1u << LB_K_SP)));
+    k_surf_grad<<<lb_div_up(N, 128), 128, 0, c->stream>>>(N, c->np, pot, c->dDu, c->dDv, c->ginv, c->Xu, c->Xv,
+                                                            pot + 2 * N, c->nrm, dout + (int64_t)r * 3 * N);
+    LB_LAUNCH(c);
+  }
+  return lb_stage_out_finish(c, out, dout, nrhs * 3 * N * sizeof(double));
+}
+
+// H = F - grad a - n x grad b, and n x H
+__global__ void k_hodge(int64_t N, const double* __restrict__ F, const double* __restrict__ ga,
+                        const double* __restrict__ gb, const double* __restrict__ nrm, double* __restrict__ H,
+                        double* __restrict__ nH) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* n = nrm + 3 * i;
+  const double* b = gb + 3 * i;
+  const double nb0 = n[1] * b[2] - n[2] * b[1], nb1 = n[2] * b[0] - n[0] * b[2], nb2 = n[0] * b[1] - n[1] * b[0];
+  const double h0 = F[3 * i] - ga[3 * i] - nb0;
+  const double h1 = F[3 * i + 1] - ga[3 * i + 1] - nb1;
+  const double h2 = F[3 * i + 2] - ga[3 * i + 2] - nb2;
+  H[3 * i] = h0; H[3 * i + 1] = h1; H[3 * i + 2] = h2;
+  nH[3 * i] = n[1] * h2 - n[2] * h1;
+  nH[3 * i + 1] = n[2] * h0 - n[0] * h2;
+  nH[3 * i + 2] = n[0] * h1 - n[1] * h0;
+}
+
+extern "C" int lb_harmonic_fields(lb_ctx* c, int nF, const double* F, double* H, lb_solve_info* info) {
+  LB_CHECK(lb_require_corr(c));
+  if (nF < 1) return lb_fail(c, LB_EINVAL, "nF must be >= 1");
+  LB_CUDA(c, cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  const double* dF;
+  double* dH;
+  LB_CHECK(lb_stage_in(c, F, nF * 3 * N * sizeof(double), c->ws_stage_in, (const void**)&dF));
+  LB_CHECK(lb_stage_out(c, H, 2 * nF * 3 * N * sizeof(double), c->ws_stage_out, (void**)&dH));
+  // per field: rhs (2N), potentials (2N), gradients (6N)
+  size_t need = (size_t)(2 * N * nF + 2 * N * nF + 6 * N) * sizeof(double);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, need) != cudaSuccess) return lb_fail(c, LB_ENOMEM, "harmonic-field workspace");
+  double* rhs = (double*)mem;                 // [2 nF][N]
+  double* pots = rhs + 2 * N * nF;            // [2 nF][N]
+  double* grads = pots + 2 * N * nF;          // [2][N][3]
+  int rc = LB_OK;
+  for (int k = 0; k < nF && rc == LB_OK; ++k) {
+    rc = surface_div_dev(c, dF + (int64_t)k * 3 * N, 0, 1.0, rhs + (int64_t)(2 * k) * N);
+    if (rc == LB_OK) rc = surface_div_dev(c, dF + (int64_t)k * 3 * N, 1, -1.0, rhs + (int64_t)(2 * k + 1) * N);
+  }
+  lb_solve_info local{};
+  if (rc == LB_OK) {
+    if (info) { *info = lb_solve_info{}; info->converged = 1; info->nrhs = 2 * nF; }
+    lb_pair_counter = 0;
+    lb_apply64_counter = lb_apply32_counter = 0;
+    rc = solve_batch(c, 2 * nF, rhs, pots, info ? info : &local);
+    if (info) { info->pairs = lb_pair_counter; info->applies_fp64 = lb_apply64_counter; info->applies_fp32 = lb_apply32_counter; }
+  }
+  for (int k = 0; k < nF && rc == LB_OK; ++k) {
+    for (int s = 0; s < 2; ++s) {
+      k_surf_grad<<<lb_div_up(N, 128), 128, 0, c->stream>>>(N, c->np, pots + (int64_t)(2 * k + s) * N, c->dDu,
+                                                              c->dDv, c->ginv, c->Xu, c->Xv, nullptr, c->nrm,
+                                                              grads + (int64_t)s * 3 * N);
+      ++c->launches;
+    }
+    k_hodge<<<lb_div_up(N, 128), 128, 0, c->stream>>>(N, dF + (int64_t)k * 3 * N, grads, grads + 3 * N, c->nrm,
+                                                        dH + (int64_t)(2 * k) * 3 * N, dH + (int64_t)(2 * k + 1) * 3 * N);
+    ++c->launches;
+    if (cudaGetLastError() != cudaSuccess) rc = lb_fail(c, LB_ECUDA, "harmonic-field kernel launch failed");
+  }
+  cudaStreamSynchronize(c->stream);
+  cudaFree(mem);
+  if (rc != LB_OK) return rc;
+  LB_CHECK(lb_stage_out_finish(c, H, dH, 2 * nF * 3 * N * sizeof(double)));
+  if (info && !info->converged) return lb_fail(c, LB_ENOTCONVERGED, "GMRES did not converge for a Hodge solve");
+  return LB_OK;
+}

@@ -263,14 +263,14 @@ def test_gmres_matches_lapack_on_random_matrix():
 
 def test_planted_sign_error_in_D_breaks_gauss(ellipsoid, monkeypatch):
     from oracle import quadrature as Q
-    orig = Q.kernel_values
+    orig = Q.kernel_values_d
 
-    def wrong(x, nx, y, ny):
-        K, r3 = orig(x, nx, y, ny)
+    def wrong(d, nx, ny):
+        K, r3 = orig(d, nx, ny)
         K = K.copy()
         K[..., 1] *= -1.0
         return K, r3
-    monkeypatch.setattr(Q, "kernel_values", wrong)
+    monkeypatch.setattr(Q, "kernel_values_d", wrong)
     g = ellipsoid.geo
     rows = np.arange(0, g.N, 97)
     v, _ = Q.build_corrections(g, ellipsoid.near_ptr, ellipsoid.near_patch, eps_q=1e-8, rows=rows)
