@@ -245,6 +245,33 @@ int lb_set_profiling(lb_ctx* ctx, int on);
  * lb_set_profiling. */
 int lb_get_profile(lb_ctx* ctx, lb_profile* out);
 
+/* Far-field sums of one density that allocate nothing: the float32 pair
+ * kernel of lb_far_sums with all of its scratch in a fixed device array that
+ * the library carries (12 MiB, held on every GPU that loads the library until
+ * the process exits).  The paper has no counterpart; this entry exists for
+ * callers that cannot allocate device memory, such as code running inside
+ * another runtime's memory pool or under a CUDA stream capture, where a
+ * cudaMalloc fails or breaks the capture.  No context is needed.
+ *   npatch, np: the surface as for lb_upload_geometry; N = npatch * np must
+ *     not exceed 65,536 (LB_EINVAL otherwise, message via lb_last_error(NULL)).
+ *   X [N][3], nrm [N][3], w [N]: node positions, unit normals, smooth weights
+ *     (device, float64; e.g. from lb_get_geometry).
+ *   sigma [N]: the density (device, float64).
+ *   row_ptr [N+1], near_patch [nnzb]: the near lists (device; e.g. from
+ *     lb_get_corrections); the sums skip exactly those (row, patch) pairs.
+ *   out [4][N]: S, D, S', S''+D' far sums (device, float64), as lb_far_sums
+ *     with LB_FP32.
+ *   stream: cudaStream_t for every launch (NULL = legacy default stream).
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one array and overwrites it: calls that may overlap on the
+ * GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  Returns LB_ECUDA if the lookup or a launch
+ * fails.  No cudaMalloc, cudaFree or allocating library call is made. */
+int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, const double* nrm, const double* w,
+                        const double* sigma, const int64_t* row_ptr, const int32_t* near_patch,
+                        double* out, void* stream);
+
 /* Surface divergence of tangential fields F [nrhs][N][3] -> out [nrhs][N]
  * (Section 2; host or device).  Used for the Hodge right-hand sides and to
  * check harmonic fields (div H = 0). */

@@ -92,6 +92,7 @@ def _load():
         "lb_solve_lb": [P, ctypes.c_int, P, P, P], "lb_harmonic_fields": [P, ctypes.c_int, P, P, P],
         "lb_surface_div": [P, ctypes.c_int, P, P],
         "lb_set_profiling": [P, ctypes.c_int], "lb_get_profile": [P, P],
+        "lb_far_sums_noalloc": [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

@@ -34,6 +34,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -636,4 +637,133 @@ extern "C" int lb_apply_A(lb_ctx* c, int nrhs, const double* tau, double* out) {
   for (int r = 0; r < nrhs; ++r)
     LB_CHECK(lb_apply_op(c, c->params.formulation, pair_prec(c), din + r * N, dout + r * N));
   return lb_stage_out_finish(c, out, dout, nrhs * N * sizeof(double));
+}
+
+// ---------------------------------------------------------------------------
+// Far sums without allocation.
+//
+// For callers that cannot allocate device memory themselves: code running
+// inside another framework's memory pool, or under a stream capture, where a
+// cudaMalloc would fail or would break the capture.  Same float32 far-field
+// kernel as lb_far_sums, with every piece of scratch (packed sources, the
+// near-tile flag table, split partials) in one file-scope device array of
+// fixed size.  Every GPU that loads the library holds this array until the
+// process exits.
+
+#define LB_NOALLOC_MAX_N 65536                      // nodes
+#define LB_NOALLOC_SPLITS 4                         // source splits (partials)
+#define LB_NOALLOC_TB 512                           // targets per block of the float32 kernel
+#define LB_NOALLOC_TS 128                           // sources per tile of the float32 kernel
+#define LB_NOALLOC_BYTES (12u << 20)                // 12 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LB_NOALLOC_BYTES];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[64] = {nullptr};
+
+// mean node position (one block, fixed order) to recentre the float32 coordinates
+__global__ void k_noalloc_center(int64_t N, const double* __restrict__ X, double* __restrict__ c) {
+  __shared__ double sh[3][256];
+  double a[3] = {0, 0, 0};
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+    for (int k = 0; k < 3; ++k) a[k] += X[3 * i + k];
+  for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] = a[k];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) {
+      double t = 0;
+      for (int j = 0; j < (int)blockDim.x; ++j) t += sh[k][j];
+      c[k] = t / (double)N;
+    }
+}
+
+// A = (x - c, w sigma), B = (n, 0); padding far away with zero charge
+__global__ void k_noalloc_pack(int64_t N, int64_t Npad, const double* __restrict__ X, const double* __restrict__ n,
+                               const double* __restrict__ w, const double* __restrict__ sigma,
+                               const double* __restrict__ c, float4* __restrict__ A, float4* __restrict__ B) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Npad) return;
+  if (i < N) {
+    A[i] = make_float4((float)(X[3 * i] - c[0]), (float)(X[3 * i + 1] - c[1]), (float)(X[3 * i + 2] - c[2]),
+                       (float)(w[i] * sigma[i]));
+    B[i] = make_float4((float)n[3 * i], (float)n[3 * i + 1], (float)n[3 * i + 2], 0.f);
+  } else {
+    A[i] = make_float4(1e15f, 1e15f, 1e15f, 0.f);
+    B[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Address of the scratch array on the current device, looked up once per
+// device (host code cannot use the array's name as a device pointer).
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return lb_fail(nullptr, LB_ECUDA, "lb_far_sums_noalloc: no current CUDA device");
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return lb_fail(nullptr, LB_ECUDA, "lb_far_sums_noalloc: cudaGetSymbolAddress failed: %s",
+                     cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return LB_OK;
+}
+
+extern "C" int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, const double* nrm, const double* w,
+                                   const double* sigma, const int64_t* row_ptr, const int32_t* near_patch,
+                                   double* out, void* stream) {
+  if (npatch < 1 || np < 3 || !X || !nrm || !w || !sigma || !row_ptr || !near_patch || !out)
+    return lb_fail(nullptr, LB_EINVAL, "lb_far_sums_noalloc: null pointer, npatch < 1 or np < 3");
+  const int64_t N = npatch * np;
+  if (N > LB_NOALLOC_MAX_N)
+    return lb_fail(nullptr, LB_EINVAL, "lb_far_sums_noalloc: N = %lld nodes exceeds the maximum of %d",
+                   (long long)N, LB_NOALLOC_MAX_N);
+  void* base = nullptr;
+  LB_CHECK(noalloc_scratch(&base));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t Npad = ((N + 1023) / 1024) * 1024;
+  const int64_t ntb = (N + LB_NOALLOC_TB - 1) / LB_NOALLOC_TB;
+  const int64_t ntiles = Npad / LB_NOALLOC_TS;
+  const int64_t nsplit = std::min<int64_t>(LB_NOALLOC_SPLITS, ntiles);
+  const int tps = (int)((ntiles + nsplit - 1) / nsplit);
+  // carve the array: centre | A | B | flags | partials (256-byte aligned pieces)
+  auto align = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char* p = (char*)base;
+  size_t off = 0;
+  double* cen = (double*)(p + off); off = align(off + 4 * sizeof(double));
+  float4* A = (float4*)(p + off); off = align(off + Npad * sizeof(float4));
+  float4* B = (float4*)(p + off); off = align(off + Npad * sizeof(float4));
+  uint8_t* flags = (uint8_t*)(p + off); off = align(off + (size_t)(ntb * ntiles));
+  double* part = (double*)(p + off); off = align(off + (size_t)(nsplit * 4 * N) * sizeof(double));
+  if (off > LB_NOALLOC_BYTES)
+    return lb_fail(nullptr, LB_EINVAL, "lb_far_sums_noalloc: scratch of %zu bytes exceeds %u", off,
+                   LB_NOALLOC_BYTES);
+  // the flag table is the only piece that must start at zero
+  cudaError_t e = cudaMemsetAsync(flags, 0, (size_t)(ntb * ntiles), st);
+  if (e != cudaSuccess) return lb_fail(nullptr, LB_ECUDA, "lb_far_sums_noalloc: %s", cudaGetErrorString(e));
+  k_noalloc_center<<<1, 256, 0, st>>>(N, X, cen);
+  k_noalloc_pack<<<lb_div_up(Npad, 256), 256, 0, st>>>(N, Npad, X, nrm, w, sigma, cen, A, B);
+  k_mask_flags<<<lb_div_up(N, 256), 256, 0, st>>>(N, np, LB_NOALLOC_TB, LB_NOALLOC_TS, ntiles, row_ptr, near_patch,
+                                                    flags);
+  dim3 grid((unsigned)ntb, (unsigned)nsplit);
+  k_far<float, FAR_KALL, 4, 128, LB_NOALLOC_TS><<<grid, 128, 0, st>>>(N, np, A, B, A, B, flags, ntiles, row_ptr,
+                                                                      near_patch, tps, part);
+  EpiSpec sp{};
+  sp.nout = 4;
+  for (int k = 0; k < 4; ++k) {
+    sp.acc[k] = k;
+    sp.scale[k] = (k == LB_K_SP) ? -LB_INV4PI : LB_INV4PI;
+    sp.kern[k] = -1;
+    sp.out[k] = out + (int64_t)k * N;
+  }
+  k_epilogue<<<lb_div_up(N * 32, 256), 256, 0, st>>>(N, np, (int)nsplit, 4, part, nrm, row_ptr, near_patch,
+                                                     nullptr, sp);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return lb_fail(nullptr, LB_ECUDA, "lb_far_sums_noalloc launch: %s", cudaGetErrorString(e));
+  return LB_OK;
 }
