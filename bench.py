@@ -152,7 +152,11 @@ def run_ours(args):
     import paper_2111_10743_gb300 as lb
     from workloads.configs import config
 
-    w = config(2)
+    if args.case == "small":   # same code path on 320 patches (N = 14,400), for profiler captures
+        from workloads.configs import ellipsoid_gauss
+        w = ellipsoid_gauss(2, 8, 1002)
+    else:
+        w = config(2)
     s = w.surface
     prec = {"fp32_refined": lb.LB_FP32_REFINED, "fp64": lb.LB_FP64, "fp32": lb.LB_FP32}[args.precision]
     params = lb.default_params(eps_quad=1e-12, tol=1e-10, precision=prec, formulation=lb.LB_A3)
@@ -200,7 +204,7 @@ def run_ours(args):
     fh = torch.tensor(w.f).pin_memory()
     uh = torch.empty_like(fh).pin_memory()
     e2e_ms = []
-    for k in range(max(1, min(args.steps, 3))):
+    for k in range(max(1, min(args.steps, args.e2e_steps))):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -247,7 +251,8 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pairs + f64 solve" if prec != lb.LB_FP64 else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32_refined": "f32 + double-float pairs, f64 solve", "fp64": "f64",
+                  "fp32": "f32 pairs, f64 solve"}[args.precision],
         "data": "synthetic", "time_to_solve_ms": round(ms_step, 3), "t_q_s": round(t_q, 2),
         "config": {"workload": WORKLOAD, "N": s.N, "patches": s.npatch, "order": s.order,
                    "formulation": "A3", "precision": args.precision, "tol": 1e-10, "eps_quad": 1e-12,
@@ -345,6 +350,9 @@ def main():
     ap.add_argument("--precision", default="fp32_refined", choices=["fp32_refined", "fp64", "fp32"])
     ap.add_argument("--cpu-targets", type=int, default=0, help="oracle sample size (0: every target)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="full: the benchmark surface; small: 320 patches of the same kind (profiling)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -52,7 +52,10 @@ extern "C" {
 /* arithmetic of the far-field pair sums (the rest of the path is float64) */
 #define LB_FP64 0          /* float64 pairs */
 #define LB_FP32 1          /* float32 pairs, compensated accumulation */
-#define LB_FP32_REFINED 2  /* solve: float32 inner GMRES inside float64 refinement */
+#define LB_FP32_REFINED 2  /* solve: float32 inner GMRES inside refinement whose residual and
+                              solution potentials use LB_DF64 pair sums */
+#define LB_DF64 3          /* double-float pairs: every quantity as a float32 pair hi + lo,
+                              error-free transformations, about 1e-14 relative */
 
 /* integral-equation formulation (Section 4, Table 2) */
 #define LB_A2 2   /* u = S[sigma]:   -sigma/4 + D^2 - S(S''+D'+2HS') + SWS = S[f]  */
@@ -70,7 +73,7 @@ typedef struct lb_ctx lb_ctx;   /* opaque */
 typedef struct {
   double eps_quad;      /* near-field quadrature tolerance (Section 6: epsilon); default 1e-12 */
   double near_factor;   /* eta: patch P is near node x when |x - c_P| < eta * R_P; default 2 */
-  int precision;        /* LB_FP64, LB_FP32 or LB_FP32_REFINED; default LB_FP64 */
+  int precision;        /* LB_FP64, LB_FP32, LB_FP32_REFINED or LB_DF64; default LB_FP64 */
   int formulation;      /* LB_A3 or LB_A2; default LB_A3 */
   int max_iter;         /* GMRES iteration cap (Section 6 caps at 100); default 100 */
   double tol;           /* relative residual target |b - A x| / |b|; default 1e-10 */
@@ -82,7 +85,7 @@ typedef struct {
   int32_t iterations;       /* total GMRES iterations (inner iterations when refined) */
   int32_t refinements;      /* outer refinement steps (0 for a plain solve) */
   int32_t converged;        /* 1 if every right-hand side reached tol */
-  int32_t applies_fp64;     /* operator applies with float64 pair sums */
+  int32_t applies_fp64;     /* operator applies with float64 or double-float pair sums */
   int32_t applies_fp32;     /* operator applies with float32 pair sums */
   int32_t nrhs;
   double rel_residual;      /* worst final relative residual over the batch (float64 apply) */
@@ -176,7 +179,7 @@ int lb_get_corrections(lb_ctx* ctx, int64_t* row_ptr, int32_t* patch, double* va
 /* Far-field sums alone (Section 4: the target-independent smooth rule over
  * all sources outside Near(i)): out [nrhs][4][N] (host or device) receives
  * sum_{j far} w_j K(x_i, x_j) sigma_j for K = S, D, S', S''+D', computed with
- * `precision` (LB_FP64 or LB_FP32).  sigma [nrhs][N] host or device. */
+ * `precision` (LB_FP64, LB_FP32 or LB_DF64).  sigma [nrhs][N] host or device. */
 int lb_far_sums(lb_ctx* ctx, int precision, int nrhs, const double* sigma, double* out);
 
 /* Discretised potentials, far sum + near corrections (Section 4):
@@ -202,8 +205,9 @@ int lb_apply_A(lb_ctx* ctx, int nrhs, const double* tau, double* out);
  * Euclidean norm, at most max_iter iterations) solves A sigma = b with
  * b = f (A3) or b = S[f] (A2), and u = S[S[sigma]] (A3) or S[sigma] (A2).
  * f, u [nrhs][N]: host or device.  info may be NULL.
- * Precision LB_FP32_REFINED runs float32 inner GMRES inside a float64
- * iterative refinement of the residual b - A sigma.
+ * Precision LB_FP32_REFINED runs float32 inner GMRES inside an iterative
+ * refinement whose residual b - A sigma (and the potentials giving u) use
+ * double-float pair sums.
  * Returns LB_ENOTCONVERGED (with u from the best iterate) when tol is not
  * reached. */
 int lb_solve_lb(lb_ctx* ctx, int nrhs, const double* f, double* u, lb_solve_info* info);
@@ -231,6 +235,10 @@ int lb_harmonic_fields(lb_ctx* ctx, int nF, const double* F, double* H, lb_solve
 #define LB_PROF_FAR64_K4 7
 #define LB_PROF_EPILOGUE 8     /* split reduction + near-field correction SpMV */
 #define LB_PROF_QUAD 9         /* correction build */
+#define LB_PROF_FARDF_K1 10    /* the four pair kernels in double-float arithmetic */
+#define LB_PROF_FARDF_KALL 11
+#define LB_PROF_FARDF_K2 12
+#define LB_PROF_FARDF_K4 13
 #define LB_PROF_NCAT 16
 
 typedef struct {

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgblb.so")
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENOTCONVERGED, LB_ETIMEOUT, LB_EGEOM, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
-LB_FP64, LB_FP32, LB_FP32_REFINED = 0, 1, 2
+LB_FP64, LB_FP32, LB_FP32_REFINED, LB_DF64 = 0, 1, 2, 3
 LB_A2, LB_A3 = 2, 3
 LB_K_S, LB_K_D, LB_K_SP, LB_K_SPPDP = 0, 1, 2, 3
 NKERNELS = 4
@@ -58,7 +58,8 @@ class lb_geom_info(ctypes.Structure):
 
 PROF_NCAT = 16
 PROF_NAMES = {0: "far32_k1", 1: "far32_kall", 2: "far32_k2", 3: "far32_k4", 4: "far64_k1", 5: "far64_kall",
-              6: "far64_k2", 7: "far64_k4", 8: "epilogue_spmv", 9: "quad"}
+              6: "far64_k2", 7: "far64_k4", 8: "epilogue_spmv", 9: "quad", 10: "fardf_k1", 11: "fardf_kall",
+              12: "fardf_k2", 13: "fardf_k4"}
 
 
 class lb_profile(ctypes.Structure):

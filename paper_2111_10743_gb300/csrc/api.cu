@@ -170,7 +170,7 @@ static int check_params(lb_ctx* c, const lb_params* p) {
   if (!(p->eps_quad > 0 && p->eps_quad < 1)) return lb_fail(c, LB_EINVAL, "eps_quad must be in (0,1)");
   if (!(p->near_factor > 1.0 && p->near_factor < 1e3))
     return lb_fail(c, LB_EINVAL, "near_factor must be in (1, 1000): the own patch must be near");
-  if (p->precision < LB_FP64 || p->precision > LB_FP32_REFINED) return lb_fail(c, LB_EINVAL, "bad precision");
+  if (p->precision < LB_FP64 || p->precision > LB_DF64) return lb_fail(c, LB_EINVAL, "bad precision");
   if (p->formulation != LB_A2 && p->formulation != LB_A3) return lb_fail(c, LB_EINVAL, "bad formulation");
   if (p->max_iter < 1 || p->max_iter > 1000) return lb_fail(c, LB_EINVAL, "max_iter must be in [1,1000]");
   if (!(p->tol > 0 && p->tol < 1)) return lb_fail(c, LB_EINVAL, "tol must be in (0,1)");
@@ -451,6 +451,16 @@ extern "C" int lb_upload_geometry(lb_ctx* c, int64_t npatch, int order, const do
   }
   for (int k = 0; k < 3; ++k) c->center[k] = cc[k] / npatch;
   c->area = a;
+  // double-float grid: 2^e bounds every recentred coordinate, h = 2^(e-23), so
+  // that differences of grid values (at most 2^(e+1) = 2^24 h) are exact floats
+  double ext = 0;
+  {
+    std::vector<double> rad(npatch);
+    LB_CUDA(c, cudaMemcpy(rad.data(), c->rad, npatch * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t P = 0; P < npatch; ++P)
+      for (int k = 0; k < 3; ++k) ext = std::max(ext, std::fabs(cen[3 * P + k] - c->center[k]) + rad[P]);
+  }
+  c->df_grid = std::ldexp(1.0, (int)std::ceil(std::log2(std::max(ext, 1e-300))) - 23);
   k_pack_sources<<<lb_div_up(c->Npad, 256), 256, 0, c->stream>>>(N, c->Npad, c->X, c->nrm, c->center[0],
                                                                    c->center[1], c->center[2], c->pos32,
                                                                    c->nrm32, c->pos64, c->nrm64);

@@ -227,7 +227,7 @@ __global__ void k_mask_flags(int64_t N, int np, int tb, int ts, int64_t ntiles, 
   }
 }
 
-static int get_mask(lb_ctx* c, int tb, int ts, MaskTable** out) {
+int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out) {
   for (auto& m : c->masks)
     if (m.tb == tb && m.ts == ts) {
       *out = &m;
@@ -254,7 +254,7 @@ static int launch_far_t(lb_ctx* c, const void* srcA, const void* srcB, double* p
   const int tb = NT * NTH;
   if (c->np * 62 < TS) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
   MaskTable* m = nullptr;
-  LB_CHECK(get_mask(c, tb, TS, &m));
+  LB_CHECK(lb_get_mask(c, tb, TS, &m));
   const int64_t ntb = m->ntb, ntiles = m->ntiles;
   // enough CTAs for several per SM: split the source range
   const int64_t want = 6LL * c->sm_count;
@@ -274,6 +274,7 @@ static int launch_far_t(lb_ctx* c, const void* srcA, const void* srcB, double* p
 }
 
 int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* srcB, double* part, int* nsplit) {
+  if (prec == LB_DF64) return lb_far_launch_df(c, kind, srcA, part, nsplit);
   if (prec == LB_FP64) {
     switch (kind) {
       case FAR_K1: return launch_far_t<double, FAR_K1, 2, 128, 64>(c, srcA, srcB, part, nsplit);
@@ -312,6 +313,12 @@ __global__ void k_pack(int64_t N, int64_t Npad, const typename V4T<R>::type* __r
 }
 
 static int pack_sources(lb_ctx* c, int prec, const double* d1, const double* d2, void** A, void** B) {
+  if (prec == LB_DF64) {  // four float4 planes
+    LB_CHECK(lb_ensure(c, c->ws_src, 4 * c->Npad * sizeof(float4)));
+    *A = c->ws_src.p;
+    *B = nullptr;
+    return lb_pack_df(c, d1, d2, *A);
+  }
   const size_t v4 = prec == LB_FP64 ? sizeof(double4_32a) : sizeof(float4);
   LB_CHECK(lb_ensure(c, c->ws_src, 2 * c->Npad * v4));
   *A = c->ws_src.p;
@@ -505,7 +512,7 @@ int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double*
   LB_CHECK(part_buffer(c, &part));
   void *A, *B;
   int nsplit = 0;
-  if (prec == LB_FP64) ++lb_apply64_counter; else ++lb_apply32_counter;
+  if (prec == LB_FP32) ++lb_apply32_counter; else ++lb_apply64_counter;
   const unsigned nb = 4 * (unsigned)std::min<int64_t>(c->sm_count, lb_div_up(N, 256));
   if (formulation == LB_A3) {
     // pass 1: charge tau -> S tau, S' tau
@@ -564,13 +571,17 @@ int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double*
 
 // ---------------------------------------------------------------------------
 // public entry points
-static int pair_prec(lb_ctx* c) { return c->params.precision == LB_FP64 ? LB_FP64 : LB_FP32; }
+static int pair_prec(lb_ctx* c) {
+  const int p = c->params.precision;
+  return (p == LB_FP64 || p == LB_DF64) ? p : LB_FP32;
+}
 
 extern "C" int lb_far_sums(lb_ctx* c, int precision, int nrhs, const double* sigma, double* out) {
   if (!c) return lb_fail(nullptr, LB_EINVAL, "null context");
   if (!c->have_geom) return lb_fail(c, LB_ESTATE, "no geometry uploaded");
   if (!c->have_near) LB_CHECK(lb_build_near(c));
-  if (nrhs < 1 || (precision != LB_FP64 && precision != LB_FP32)) return lb_fail(c, LB_EINVAL, "bad nrhs/precision");
+  if (nrhs < 1 || (precision != LB_FP64 && precision != LB_FP32 && precision != LB_DF64))
+    return lb_fail(c, LB_EINVAL, "bad nrhs/precision");
   LB_CUDA(c, cudaSetDevice(c->device));
   const int64_t N = c->N;
   const double* din;

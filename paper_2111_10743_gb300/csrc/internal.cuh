@@ -54,6 +54,7 @@ struct lb_ctx {
   std::vector<double> ref_uv, ref_w;       // host copies of the node rule
   std::vector<double> Vinv, Du, Dv;        // [np][np] host, row-major
   double center[3] = {0, 0, 0};            // mean node position (float32 recentring)
+  double df_grid = 0;                      // double-float position grid (power of two)
   double area = 0;
 
   double* X = nullptr;     // [N][3]
@@ -166,6 +167,9 @@ int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* s
 int lb_potentials(lb_ctx* c, int prec, const double* sigma, double* pot, unsigned which);
 // apply the formulation operator to one vector (device in, device out)
 int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double* out);
+int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out);
+int lb_pack_df(lb_ctx* c, const double* d1, const double* d2, void* S);
+int lb_far_launch_df(lb_ctx* c, int kind, const void* S, double* part, int* nsplit);
 // weighted mean of a device vector (deterministic), result to host
 int lb_wmean(lb_ctx* c, const double* f, double* mean_host);
 // counters of the last solve

@@ -12,7 +12,9 @@
 //
 // Mixed precision (LB_FP32_REFINED): float32 pair sums are accurate to about
 // 1e-6, so an inner GMRES on the float32 operator to inner_tol is wrapped in
-// iterative refinement whose residual b - A x uses float64 pair sums.
+// iterative refinement whose residual b - A x uses double-float pair sums
+// (about 1e-14, several times faster than float64 on GB300); the solution
+// potentials u = S[S[sigma]] use them too.
 //
 // Surface operators (Section 2), by nodal differentiation within a patch:
 //   grad_Gamma f = (g^11 f_u + g^12 f_v) X_u + (g^21 f_u + g^22 f_v) X_v,
@@ -287,8 +289,19 @@ static int apply_S_dev(lb_ctx* c, int prec, const double* s, double* out) {
   return LB_OK;
 }
 
-// one right-hand side: b (device) -> sigma (device)
-static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch, lb_solve_info* info, int first) {
+// one right-hand side: b (device) -> sigma (device).  In the refined mode the
+// solution potential u is produced here too (u_out), otherwise by the caller.
+//
+// Refinement (LB_FP32_REFINED), standard iterative refinement with the
+// residual in higher precision where it matters:
+//   x1 = GMRES32(b); r1 = b - A_df x1 (the one double-float apply; its second
+//   pass also yields S^2 x1 for A3, its first S x1 for A2);
+//   then x_{k+1} = x_k + GMRES32(r_k), r_{k+1} = r_k - A32 delta: delta is
+//   about inner_tol |x|, so float32 pairs (relative 1e-7) keep this update
+//   accurate to about 1e-7 inner_tol |b|;
+//   u = (S^2 x1 or S x1) + S32-potential of (x - x1), for the same reason.
+static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch, lb_solve_info* info, int first,
+                     double* u_out) {
   const int64_t N = c->N;
   const lb_params& p = c->params;
   std::vector<double> hist;
@@ -303,13 +316,17 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
       info->rel_residual = std::max(info->rel_residual, res);
     }
   } else {
-    // iterative refinement: sigma = 0, r = b; repeat  delta = GMRES32(r); sigma += delta; r = b - A64 sigma
     double* r = scratch;
     double* delta = scratch + N;
     double* Ax = scratch + 2 * N;
+    double* x1 = scratch + 3 * N;
+    double* ux1 = scratch + 4 * N;
+    double* tmp = scratch + 5 * N;
     double nbv = 0, rn = 0;
     LB_CHECK(norm2(c, b, &nbv));
     LB_CUDA(c, cudaMemsetAsync(sigma, 0, N * sizeof(double), c->stream));
+    LB_CUDA(c, cudaMemsetAsync(x1, 0, N * sizeof(double), c->stream));
+    LB_CUDA(c, cudaMemsetAsync(ux1, 0, N * sizeof(double), c->stream));
     LB_CUDA(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     bool ok = nbv == 0.0;
     int steps = 0;
@@ -322,10 +339,21 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
       it += its;
       k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, delta, 1.0, sigma);
       LB_LAUNCH(c);
-      LB_CHECK(lb_apply_op(c, p.formulation, LB_FP64, sigma, Ax));
-      LB_CUDA(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, Ax, 1.0, r);
-      LB_LAUNCH(c);
+      if (s == 0) {
+        // r = b - A x1 in double-float; keep x1 and its solution potential
+        LB_CHECK(lb_apply_op(c, p.formulation, LB_DF64, sigma, Ax));
+        const double* pot = (const double*)c->ws_pot.p;  // [4][N] of the last apply
+        LB_CUDA(c, cudaMemcpyAsync(ux1, p.formulation == LB_A3 ? pot + N : pot, N * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, c->stream));
+        LB_CUDA(c, cudaMemcpyAsync(x1, sigma, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        LB_CUDA(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, Ax, 1.0, r);
+        LB_LAUNCH(c);
+      } else {
+        LB_CHECK(lb_apply_op(c, p.formulation, LB_FP32, delta, Ax));
+        k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, Ax, 1.0, r);
+        LB_LAUNCH(c);
+      }
       LB_CHECK(norm2(c, r, &rn));
       rel = rn / nbv;
       ++steps;
@@ -339,6 +367,17 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
       info->converged = info->converged && ok;
       info->rel_residual = std::max(info->rel_residual, rel);
     }
+    if (u_out) {  // u = u(x1) + float32 potential of x - x1
+      LB_CUDA(c, cudaMemcpyAsync(tmp, sigma, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, x1, 1.0, tmp);
+      LB_LAUNCH(c);
+      LB_CHECK(apply_S_dev(c, LB_FP32, tmp, Ax));
+      if (p.formulation == LB_A3) LB_CHECK(apply_S_dev(c, LB_FP32, Ax, tmp));
+      else LB_CUDA(c, cudaMemcpyAsync(tmp, Ax, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      LB_CUDA(c, cudaMemcpyAsync(u_out, ux1, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, tmp, 1.0, u_out);
+      LB_LAUNCH(c);
+    }
   }
   if (info && first) {
     info->history_len = (int32_t)std::min<size_t>(hist.size(), 128);
@@ -350,13 +389,13 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
 static int solve_batch(lb_ctx* c, int nrhs, const double* f, double* u, lb_solve_info* info) {
   const int64_t N = c->N;
   const lb_params& p = c->params;
-  LB_CHECK(lb_ensure(c, c->ws_quad, (size_t)(6 * N) * sizeof(double)));
+  LB_CHECK(lb_ensure(c, c->ws_quad, (size_t)(9 * N) * sizeof(double)));
   double* fb = (double*)c->ws_quad.p;    // projected f, then b
   double* sig = fb + N;
-  double* scratch = fb + 2 * N;          // 3 N for refinement
-  double* tmp = fb + 5 * N;
-  // solution potentials: float32 pairs only in the plain float32 mode
-  const int post = p.precision == LB_FP32 ? LB_FP32 : LB_FP64;
+  double* scratch = fb + 2 * N;          // 6 N for refinement
+  double* tmp = fb + 8 * N;
+  // solution potentials of the plain modes in their own pair arithmetic
+  const int post = p.precision == LB_FP32 ? LB_FP32 : (p.precision == LB_FP64 ? LB_FP64 : LB_DF64);
   int* dbad = nullptr;
   LB_CHECK(lb_ensure(c, c->ws_red, 4096));
   dbad = (int*)((char*)c->ws_red.p + 3072);
@@ -376,8 +415,9 @@ static int solve_batch(lb_ctx* c, int nrhs, const double* f, double* u, lb_solve
       LB_CHECK(apply_S_dev(c, post, fb, tmp));
       LB_CUDA(c, cudaMemcpyAsync(fb, tmp, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
-    LB_CHECK(solve_one(c, fb, sig, scratch, info, r == 0));
     double* ur = u + (int64_t)r * N;
+    LB_CHECK(solve_one(c, fb, sig, scratch, info, r == 0, ur));
+    if (p.precision == LB_FP32_REFINED) continue;  // u produced by the refinement
     if (p.formulation == LB_A3) {  // u = S[S[sigma]]
       LB_CHECK(apply_S_dev(c, post, sig, tmp));
       LB_CHECK(apply_S_dev(c, post, tmp, ur));
@@ -509,7 +549,8 @@ extern "C" int lb_apply_gradS(lb_ctx* c, int nrhs, const double* sigma, double* 
   LB_CHECK(lb_stage_out(c, out, nrhs * 3 * N * sizeof(double), c->ws_stage_out, (void**)&dout));
   LB_CHECK(lb_ensure(c, c->ws_quad, (size_t)(4 * N) * sizeof(double)));
   double* pot = (double*)c->ws_quad.p;
-  const int prec = c->params.precision == LB_FP64 ? LB_FP64 : LB_FP32;
+  const int pp = c->params.precision;
+  const int prec = (pp == LB_FP64 || pp == LB_DF64) ? pp : LB_FP32;
   for (int r = 0; r < nrhs; ++r) {
     LB_CHECK(lb_potentials(c, prec, din + r * N, pot, (1u << LB_K_S) | (1u << LB_K_SP)));
     k_surf_grad<<<lb_div_up(N, 128), 128, 0, c->stream>>>(N, c->np, pot, c->dDu, c->dDv, c->ginv, c->Xu, c->Xv,

@@ -92,9 +92,12 @@ def test_far_sums_fp64_fp32(lb, name):
     ref = farsum.far_sums(d.geo, d.near_ptr, d.near_patch, sig)
     got64 = ctx.far_sums(sig, precision=lb.LB_FP64)
     got32 = ctx.far_sums(sig, precision=lb.LB_FP32)
+    gotdf = ctx.far_sums(sig, precision=lb.LB_DF64)
     for k in range(4):
         assert _rel(got64[:, k], ref[:, k]) < 1e-12, k
         assert _rel(got32[:, k], ref[:, k]) < 2e-5, k
+        # double-float sums: ~1e-14 per pair; S''+D' cancels partly (measured 2.2e-12)
+        assert _rel(gotdf[:, k], ref[:, k]) < 5e-12, k
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -109,8 +112,10 @@ def test_potentials_with_oracle_corrections(lb, name):
 
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("form", ["A3", "A2"])
-def test_operators(lb, name, form):
-    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3 if form == "A3" else lb.LB_A2)
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_operators(lb, name, form, prec):
+    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3 if form == "A3" else lb.LB_A2,
+                        precision=lb.LB_FP64 if prec == "fp64" else lb.LB_DF64)
     rng = np.random.default_rng(23)
     tau = rng.standard_normal((2, d.geo.N))
     assert _rel(ctx.apply_A(tau), d.apply(form, tau)) < 1e-12
@@ -118,10 +123,12 @@ def test_operators(lb, name, form):
 
 @pytest.mark.parametrize("name", ["sphere300", "torus1920"])
 @pytest.mark.parametrize("form", ["A3", "A2"])
-def test_solve_fp64_matches_oracle(lb, name, form):
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_solve_fp64_matches_oracle(lb, name, form, prec):
     from oracle.gmres import solve_lb
     from workloads.rhs import legendre_field
-    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3 if form == "A3" else lb.LB_A2, tol=1e-12)
+    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3 if form == "A3" else lb.LB_A2, tol=1e-12,
+                        precision=lb.LB_FP64 if prec == "fp64" else lb.LB_DF64)
     f = legendre_field(d.geo.X, np.random.default_rng(24), 4, 2.75)
     u_ref, _, it_ref, _ = solve_lb(d, f, form, tol=1e-12)
     u, info = ctx.solve_lb(f[None, :])
@@ -242,7 +249,9 @@ def test_full_size_sampled_rows(lb):
     assert np.abs(vals[sel] - ov[sel]).max() < 1e-10 * np.abs(ov[sel]).max()
     sig = np.random.default_rng(30).standard_normal(g.N)
     ref = farsum.far_sums(g, ptr, pl, sig, targets=rows)[0]
-    for prec, tol in ((lb.LB_FP64, 1e-12), (lb.LB_FP32, 2e-5)):
+    # the FP64 oracle sums 57,600 terms of random sign in plain order: its own
+    # rounding is about 1e-11 of the largest sum here, which bounds the DF64 check
+    for prec, tol in ((lb.LB_FP64, 1e-12), (lb.LB_DF64, 2e-11), (lb.LB_FP32, 2e-5)):
         got = ctx.far_sums(sig, precision=prec)[0][:, rows]
         for k in range(4):
             assert _rel(got[k], ref[k]) < tol, (prec, k)
