@@ -42,7 +42,13 @@ template <typename R> struct V4T;
 template <> struct V4T<float> { typedef float4 type; };
 template <> struct V4T<double> { typedef double4_32a type; };
 
-__device__ __forceinline__ float lb_rsqrt(float x) { return rsqrtf(x); }
+// one MUFU instruction (approximate, flushes subnormals: pair distances here
+// are far from the subnormal range)
+__device__ __forceinline__ float lb_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ double lb_rsqrt(double x) { return rsqrt(x); }
 
 // float-float running total: hi + lo, updated with TwoSum (Knuth)
@@ -99,7 +105,7 @@ __device__ __forceinline__ void far_pair(const R tx, const R ty, const R tz, con
     const R ex = nx - b.x, ey = ny - b.y, ez = nz - b.z;
     const R dnd = ex * dx + ey * dy + ez * dz;
     const R dn2 = ex * ex + ey * ey + ez * ez;
-    acc[3] += b.w * rinv3 * (R(3) * nxd * dnd * rinv2 - R(0.5) * dn2);
+    acc[3] += b.w * rinv3 * ((nxd * dnd) * (R(3) * rinv2) - R(0.5) * dn2);
   } else {  // FAR_K4
     const R rinv3 = rinv * rinv * rinv;
     const R nyd = b.x * dx + b.y * dy + b.z * dz;
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(NTH) k_far(int64_t N, int np, const typename V
     __syncthreads();
     const bool any_near = flags[(int64_t)blockIdx.x * ntiles + tile] != 0;
     if (!any_near) {
-#pragma unroll 4
+#pragma unroll 8
       for (int s = 0; s < TS; ++s) {
         const V4 a = sA[s];
         const V4 b = kUseB ? sB[s] : a;
@@ -352,17 +358,38 @@ __global__ void k_epilogue(int64_t N, int np, int nsplit, int nacc, const double
   if (i >= N) return;
   double cs[4] = {0, 0, 0, 0};
   if (vals) {
-    const int64_t rb = row_ptr[i], re = row_ptr[i + 1];
-    const int64_t ne = (re - rb) * np;
-    for (int64_t e = lane; e < ne; e += 32) {
-      const int64_t bo = e / np;
-      const int q = (int)(e - bo * np);
-      const int64_t b = rb + bo;
-      const int64_t col = (int64_t)near_patch[b] * np + q;
-      const double* vb = vals + b * (LB_NKERNELS * np) + q;
+    // the row's (block, node) pairs flattened; each lane walks them 32 apart,
+    // four at a time so that their loads overlap, tracking (block, node)
+    // incrementally instead of dividing
+    const int64_t rb = row_ptr[i];
+    const int ne = (int)((row_ptr[i + 1] - rb) * np);
+    const int stride = LB_NKERNELS * np;
+    int bo = lane / np, q = lane - (lane / np) * np;
+    for (int e = lane; e < ne; e += 128) {
+      int bl[4], ql[4];
 #pragma unroll
-      for (int o = 0; o < 4; ++o)
-        if (o < sp.nout && sp.kern[o] >= 0) cs[o] = fma(vb[sp.kern[o] * np], sp.dens[o][col], cs[o]);
+      for (int u = 0; u < 4; ++u) {
+        bl[u] = bo;
+        ql[u] = q;
+        q += 32;
+        while (q >= np) { q -= np; ++bo; }
+      }
+      int64_t col[4];
+      const double* vb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = e + 32 * u < ne;
+        const int64_t b = rb + (ok ? bl[u] : 0);
+        col[u] = ok ? (int64_t)near_patch[b] * np + ql[u] : -1;
+        vb[u] = vals + b * stride + ql[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (col[u] < 0) continue;
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+          if (o < sp.nout && sp.kern[o] >= 0) cs[o] = fma(__ldg(vb[u] + sp.kern[o] * np), sp.dens[o][col[u]], cs[o]);
+      }
     }
 #pragma unroll
     for (int o = 0; o < 4; ++o)

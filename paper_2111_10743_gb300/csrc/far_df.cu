@@ -52,9 +52,10 @@ __device__ __forceinline__ F2 df_scale(F2 a, float s) {  // s a power of two or 
   const float p = a.h * s;
   return fast_two_sum(p, fmaf(a.h, s, -p) + a.l * s);
 }
-// 1 / sqrt(x) with one Newton step on the float32 seed
+// 1 / sqrt(x) with one Newton step on the float32 seed (one MUFU instruction)
 __device__ __forceinline__ F2 df_rsqrt(F2 x) {
-  const float y = rsqrtf(x.h);
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x.h));
   const float yy = y * y;
   const F2 y2 = {yy, fmaf(y, y, -yy)};
   const F2 xy2 = df_mul(x, y2);
