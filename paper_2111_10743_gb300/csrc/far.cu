@@ -220,6 +220,200 @@ __global__ void __launch_bounds__(NTH) k_far(int64_t N, int np, const typename V
   }
 }
 
+// ---------------------------------------------------------------------------
+// float32 pair kernels with packed two-lane arithmetic (sm_100 family
+// f32x2 add/sub/mul/fma): each target is held splatted in both halves of a
+// 64-bit register and every instruction evaluates the target against two
+// consecutive sources, halving the issued instructions per pair (used for
+// the longer kernels K2, KALL, K4; the short K1 measured faster scalar).  Sources
+// are staged as structure-of-arrays so that consecutive pairs load directly
+// as packed operands.  Tiles with near pairs fall back to the scalar loop.
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(u64 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ u64 add2(u64 a, u64 b) { u64 r; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) { u64 r; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) { u64 r; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ u64 rsqrt2(u64 x) {
+  float a, b;
+  upk2(x, a, b);
+  return pk2(lb_rsqrt(a), lb_rsqrt(b));
+}
+
+// two pairs (one target, sources s and s+1); T: target x, y, z, nx, ny, nz
+// splatted; S: packed source components x, y, z, q1, nx, ny, nz, q2
+template <int KIND>
+__device__ __forceinline__ void pair2(const u64* T, const u64* S, u64* acc, const u64 three, const u64 mhalf) {
+  const u64 dx = sub2(T[0], S[0]), dy = sub2(T[1], S[1]), dz = sub2(T[2], S[2]);
+  const u64 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+  const u64 rinv = rsqrt2(r2);
+  if (KIND == FAR_K1) {
+    const u64 qr = mul2(S[3], rinv);
+    acc[0] = add2(acc[0], qr);
+    const u64 t = mul2(qr, mul2(rinv, rinv));
+    acc[1] = fma2(t, dx, acc[1]);
+    acc[2] = fma2(t, dy, acc[2]);
+    acc[3] = fma2(t, dz, acc[3]);
+    return;
+  }
+  const u64 rinv2 = mul2(rinv, rinv);
+  const u64 rinv3 = mul2(rinv2, rinv);
+  if (KIND == FAR_K4) {
+    const u64 nyd = fma2(S[6], dz, fma2(S[5], dy, mul2(S[4], dx)));
+    acc[0] = fma2(mul2(S[3], rinv3), nyd, acc[0]);
+    acc[1] = fma2(S[7], rinv, acc[1]);
+    return;
+  }
+  const u64 nxd = fma2(T[5], dz, fma2(T[4], dy, mul2(T[3], dx)));
+  const u64 ex = sub2(T[3], S[4]), ey = sub2(T[4], S[5]), ez = sub2(T[5], S[6]);
+  const u64 dnd = fma2(ez, dz, fma2(ey, dy, mul2(ex, dx)));
+  const u64 dn2 = fma2(ez, ez, fma2(ey, ey, mul2(ex, ex)));
+  const u64 kk = fma2(mul2(nxd, dnd), mul2(three, rinv2), mul2(mhalf, dn2));
+  if (KIND == FAR_KALL) {
+    const u64 qr3 = mul2(S[3], rinv3);
+    const u64 nyd = sub2(nxd, dnd);
+    acc[0] = fma2(S[3], rinv, acc[0]);
+    acc[1] = fma2(qr3, nyd, acc[1]);
+    acc[2] = fma2(qr3, nxd, acc[2]);
+    acc[3] = fma2(qr3, kk, acc[3]);
+  } else {  // FAR_K2
+    const u64 t = mul2(nxd, rinv3);
+    acc[0] = fma2(S[3], t, acc[0]);
+    acc[1] = fma2(S[7], rinv, acc[1]);
+    acc[2] = fma2(S[7], t, acc[2]);
+    acc[3] = fma2(mul2(S[7], rinv3), kk, acc[3]);
+  }
+}
+
+template <int KIND, int NT, int NTH, int TS>
+__global__ void __launch_bounds__(NTH) k_far32x2(int64_t N, int np, const float4* __restrict__ tpos,
+                                                 const float4* __restrict__ tnrm, const float4* __restrict__ srcA,
+                                                 const float4* __restrict__ srcB, const uint8_t* __restrict__ flags,
+                                                 int64_t ntiles, const int64_t* __restrict__ row_ptr,
+                                                 const int32_t* __restrict__ near_patch, int tiles_per_split,
+                                                 double* __restrict__ part) {
+  constexpr int NO = FarOut<KIND>::n;
+  constexpr bool kUseB = KIND != FAR_K1;
+  constexpr int NC = kUseB ? 8 : 4;                   // staged source components
+  constexpr bool kTN = KIND == FAR_K2 || KIND == FAR_KALL;  // target normals needed
+  __shared__ __align__(16) float sS[NC][TS];
+  __shared__ int sLp[TS];
+  const int64_t t0 = (int64_t)blockIdx.x * (NTH * NT);
+  u64 T[NT][6];
+  float tf[NT][6];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int64_t t = t0 + threadIdx.x + j * NTH;
+    const float4 p = tpos[t];
+    tf[j][0] = p.x; tf[j][1] = p.y; tf[j][2] = p.z;
+    tf[j][3] = tf[j][4] = tf[j][5] = 0.f;
+    if (kTN) {
+      const float4 q = tnrm[t];
+      tf[j][3] = q.x; tf[j][4] = q.y; tf[j][5] = q.z;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) T[j][k] = pk2(tf[j][k], tf[j][k]);
+  }
+  const u64 three = pk2(3.f, 3.f), mhalf = pk2(-0.5f, -0.5f);
+  u64 acc[NT][NO];
+  FF tot[NT][NO];
+#pragma unroll
+  for (int j = 0; j < NT; ++j)
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      acc[j][o] = 0ull;
+      tot[j][o].hi = 0.f;
+      tot[j][o].lo = 0.f;
+    }
+  const int64_t tile_b = (int64_t)blockIdx.y * tiles_per_split;
+  const int64_t tile_e = min(ntiles, tile_b + tiles_per_split);
+  for (int64_t tile = tile_b; tile < tile_e; ++tile) {
+    const int64_t s0 = tile * TS;
+    const int64_t P0 = s0 / np;
+    for (int s = threadIdx.x; s < TS; s += NTH) {
+      const float4 a = srcA[s0 + s];
+      sS[0][s] = a.x; sS[1][s] = a.y; sS[2][s] = a.z; sS[3][s] = a.w;
+      if (kUseB) {
+        const float4 b = srcB[s0 + s];
+        sS[4][s] = b.x; sS[5][s] = b.y; sS[6][s] = b.z; sS[7][s] = b.w;
+      }
+      sLp[s] = (int)((s0 + s) / np - P0);
+    }
+    __syncthreads();
+    const bool any_near = flags[(int64_t)blockIdx.x * ntiles + tile] != 0;
+    if (!any_near) {
+#pragma unroll 2
+      for (int s = 0; s < TS; s += 4) {
+        u64 S0[8], S1[8];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(&sS[c][s]);
+          S0[c] = pk2(v.x, v.y);
+          S1[c] = pk2(v.z, v.w);
+        }
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          pair2<KIND>(T[j], S0, acc[j], three, mhalf);
+          pair2<KIND>(T[j], S1, acc[j], three, mhalf);
+        }
+      }
+    } else {
+      // scalar loop with the per-target near-patch mask
+      unsigned long long m[NT];
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int64_t t = t0 + threadIdx.x + j * NTH;
+        m[j] = 0ull;
+        if (t < N)
+          for (int64_t bb = row_ptr[t]; bb < row_ptr[t + 1]; ++bb) {
+            const int64_t d = (int64_t)near_patch[bb] - P0;
+            if (d >= 0 && d < 64) m[j] |= 1ull << d;
+          }
+      }
+      for (int s = 0; s < TS; ++s) {
+        const float4 a = make_float4(sS[0][s], sS[1][s], sS[2][s], sS[3][s]);
+        const float4 b = kUseB ? make_float4(sS[4][s], sS[5][s], sS[6][s], sS[7][s]) : a;
+        const int lp = sLp[s];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          float sa[4] = {0.f, 0.f, 0.f, 0.f};
+          far_pair<float, KIND>(tf[j][0], tf[j][1], tf[j][2], tf[j][3], tf[j][4], tf[j][5], a, b,
+                                (m[j] >> lp) & 1ull, sa);
+#pragma unroll
+          for (int o = 0; o < NO; ++o) acc[j][o] = add2(acc[j][o], pk2(sa[o], 0.f));
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        float lo, hi;
+        upk2(acc[j][o], lo, hi);
+        tot[j][o].add(lo + hi);
+        acc[j][o] = 0ull;
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int64_t t = t0 + threadIdx.x + j * NTH;
+    if (t >= N) continue;
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      part[((int64_t)blockIdx.y * NO + o) * N + t] = (double)tot[j][o].hi + (double)tot[j][o].lo;
+  }
+}
+
 // flag (target block, source tile) pairs that contain a near pair
 __global__ void k_mask_flags(int64_t N, int np, int tb, int ts, int64_t ntiles, const int64_t* __restrict__ row_ptr,
                              const int32_t* __restrict__ near_patch, uint8_t* __restrict__ flags) {
@@ -279,6 +473,28 @@ static int launch_far_t(lb_ctx* c, const void* srcA, const void* srcB, double* p
   return LB_OK;
 }
 
+template <int KIND, int NT, int NTH, int TS>
+static int launch_far32x2(lb_ctx* c, const void* srcA, const void* srcB, double* part, int* nsplit_out) {
+  const int tb = NT * NTH;
+  if (c->np * 62 < TS) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
+  MaskTable* m = nullptr;
+  LB_CHECK(lb_get_mask(c, tb, TS, &m));
+  const int64_t ntb = m->ntb, ntiles = m->ntiles;
+  const int64_t want = 6LL * c->sm_count;
+  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(ntiles, (want + ntb - 1) / ntb));
+  const int tps = (int)((ntiles + nsplit - 1) / nsplit);
+  nsplit = (ntiles + tps - 1) / tps;
+  dim3 grid((unsigned)ntb, (unsigned)nsplit);
+  ProfScope prof(c, LB_PROF_FAR32_K1 + KIND);
+  k_far32x2<KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, c->np, c->pos32, c->nrm32, (const float4*)srcA,
+                                                            (const float4*)srcB, m->flags, ntiles, c->row_ptr,
+                                                            c->near_patch, tps, part);
+  LB_LAUNCH(c);
+  lb_pair_counter += c->N * c->N;
+  *nsplit_out = (int)nsplit;
+  return LB_OK;
+}
+
 int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* srcB, double* part, int* nsplit) {
   if (prec == LB_DF64) return lb_far_launch_df(c, kind, srcA, part, nsplit);
   if (prec == LB_FP64) {
@@ -291,9 +507,9 @@ int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* s
   }
   switch (kind) {
     case FAR_K1: return launch_far_t<float, FAR_K1, 4, 128, 128>(c, srcA, srcB, part, nsplit);
-    case FAR_KALL: return launch_far_t<float, FAR_KALL, 4, 128, 128>(c, srcA, srcB, part, nsplit);
-    case FAR_K2: return launch_far_t<float, FAR_K2, 4, 128, 128>(c, srcA, srcB, part, nsplit);
-    default: return launch_far_t<float, FAR_K4, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+    case FAR_KALL: return launch_far32x2<FAR_KALL, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+    case FAR_K2: return launch_far32x2<FAR_K2, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+    default: return launch_far32x2<FAR_K4, 4, 128, 128>(c, srcA, srcB, part, nsplit);
   }
 }
 

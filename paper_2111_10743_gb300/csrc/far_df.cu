@@ -33,24 +33,25 @@ __device__ __forceinline__ F2 fast_two_sum(float a, float b) {
   const float s = a + b;
   return {s, b - (s - a)};
 }
+// The pairs below are left unnormalised (no FastTwoSum after each
+// operation): hi + lo stays an exact-enough unevaluated sum with |lo| within a
+// few ulp of hi, and products drop only the lo * lo terms.
 __device__ __forceinline__ F2 df_add(F2 a, F2 b) {
-  F2 s = two_sum(a.h, b.h);
-  return fast_two_sum(s.h, s.l + (a.l + b.l));
+  const F2 s = two_sum(a.h, b.h);
+  return {s.h, s.l + (a.l + b.l)};
 }
 __device__ __forceinline__ F2 df_sub(F2 a, F2 b) { return df_add(a, {-b.h, -b.l}); }
 __device__ __forceinline__ F2 df_mul(F2 a, F2 b) {
   const float p = a.h * b.h;
-  const float e = fmaf(a.h, b.h, -p);
-  return fast_two_sum(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
+  return {p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)))};
 }
 __device__ __forceinline__ F2 df_sqr(F2 a) {
   const float p = a.h * a.h;
-  const float e = fmaf(a.h, a.h, -p);
-  return fast_two_sum(p, fmaf(2.f * a.h, a.l, e));
+  return {p, fmaf(a.h + a.h, a.l, fmaf(a.h, a.h, -p))};
 }
 __device__ __forceinline__ F2 df_scale(F2 a, float s) {  // s a power of two or small integer
   const float p = a.h * s;
-  return fast_two_sum(p, fmaf(a.h, s, -p) + a.l * s);
+  return {p, fmaf(a.h, s, -p) + a.l * s};
 }
 // 1 / sqrt(x) with one Newton step on the float32 seed (one MUFU instruction)
 __device__ __forceinline__ F2 df_rsqrt(F2 x) {
