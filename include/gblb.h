@@ -258,8 +258,9 @@ int lb_get_profile(lb_ctx* ctx, lb_profile* out);
  * the library carries (12 MiB, held on every GPU that loads the library until
  * the process exits).  The paper has no counterpart; this entry exists for
  * callers that cannot allocate device memory, such as code running inside
- * another runtime's memory pool or under a CUDA stream capture, where a
- * cudaMalloc fails or breaks the capture.  No context is needed.
+ * another runtime's memory pool that owns every allocation on the device, or
+ * a service that must keep a fixed device footprint after start-up.  No
+ * context is needed.
  *   npatch, np: the surface as for lb_upload_geometry; N = npatch * np must
  *     not exceed 65,536 (LB_EINVAL otherwise, message via lb_last_error(NULL)).
  *   X [N][3], nrm [N][3], w [N]: node positions, unit normals, smooth weights
@@ -271,7 +272,7 @@ int lb_get_profile(lb_ctx* ctx, lb_profile* out);
  *     with LB_FP32.
  *   stream: cudaStream_t for every launch (NULL = legacy default stream).
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
+ * device current) and keeps it for the later calls.  Every
  * call shares the one array and overwrites it: calls that may overlap on the
  * GPU (different streams, or different host threads) race and must be
  * serialised by the caller.  Returns LB_ECUDA if the lookup or a launch

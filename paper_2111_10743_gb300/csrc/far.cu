@@ -897,8 +897,9 @@ extern "C" int lb_apply_A(lb_ctx* c, int nrhs, const double* tau, double* out) {
 // Far sums without allocation.
 //
 // For callers that cannot allocate device memory themselves: code running
-// inside another framework's memory pool, or under a stream capture, where a
-// cudaMalloc would fail or would break the capture.  Same float32 far-field
+// inside another framework's memory pool that owns every allocation on the
+// device, or a service that must keep a fixed device footprint after
+// start-up.  Same float32 far-field
 // kernel as lb_far_sums, with every piece of scratch (packed sources, the
 // near-tile flag table, split partials) in one file-scope device array of
 // fixed size.  Every GPU that loads the library holds this array until the

@@ -2,7 +2,7 @@
 
 The entry point runs the float32 far-field kernel with its scratch in a fixed
 device array carried by the library, so that code inside another runtime's
-memory pool, or under a stream capture, can use it without cudaMalloc.  Its
+memory pool, which owns every allocation, can use it without cudaMalloc.  Its
 output is checked against the allocating entry point lb_far_sums (float32
 pairs) on two calls in a row, which also shows that the shared array is
 reset between calls.  This file is collected last and needs nothing from the
