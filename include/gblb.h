@@ -197,7 +197,9 @@ int lb_apply_SppDp(lb_ctx* ctx, int nrhs, const double* sigma, double* out);
 int lb_apply_gradS(lb_ctx* ctx, int nrhs, const double* sigma, double* out);
 
 /* The operator of the context's formulation (A3 or A2; Sections 4.2, 4.3):
- * out [nrhs][N] = A tau.  tau, out: host or device. */
+ * out [nrhs][N] = A tau.  tau, out: host or device.  With A3, nrhs >= 2 and
+ * float32 or double-float pairs, up to 8 densities share each far-field
+ * pass (the pair geometry is evaluated once for all of them). */
 int lb_apply_A(lb_ctx* ctx, int nrhs, const double* tau, double* out);
 
 /* Solve Delta_Gamma u = f for mean-zero u (Lemma 1), nrhs right-hand sides
@@ -208,6 +210,11 @@ int lb_apply_A(lb_ctx* ctx, int nrhs, const double* tau, double* out);
  * Precision LB_FP32_REFINED runs float32 inner GMRES inside an iterative
  * refinement whose residual b - A sigma (and the potentials giving u) use
  * double-float pair sums.
+ * With A3, nrhs >= 2 and any precision but LB_FP64, the right-hand sides
+ * are solved in lockstep (groups of up to 64): each GMRES iteration applies
+ * A3 to all systems still iterating in one batched pass, and each system
+ * stops at its own tolerance; info sums iterations over the right-hand
+ * sides and keeps the history of the first.
  * Returns LB_ENOTCONVERGED (with u from the best iterate) when tol is not
  * reached. */
 int lb_solve_lb(lb_ctx* ctx, int nrhs, const double* f, double* u, lb_solve_info* info);
@@ -245,6 +252,7 @@ typedef struct {
   double ms[LB_PROF_NCAT];     /* summed device time per category */
   int64_t calls[LB_PROF_NCAT]; /* timed launches per category */
   int64_t launches;            /* every kernel launched while profiling was on */
+  int64_t pairs[LB_PROF_NCAT]; /* far categories: (target, source, density) pair evaluations */
 } lb_profile;
 
 /* Turn per-kernel timing on (1) or off (0); either way the counters restart. */

@@ -64,7 +64,7 @@ PROF_NAMES = {0: "far32_k1", 1: "far32_kall", 2: "far32_k2", 3: "far32_k4", 4: "
 
 class lb_profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * PROF_NCAT), ("calls", ctypes.c_int64 * PROF_NCAT),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("pairs", ctypes.c_int64 * PROF_NCAT)]
 
 
 class LBError(RuntimeError):
@@ -197,7 +197,7 @@ class Context:
         out = {"launches": p.launches}
         for k, name in PROF_NAMES.items():
             if p.calls[k]:
-                out[name] = {"ms": p.ms[k], "calls": p.calls[k]}
+                out[name] = {"ms": p.ms[k], "calls": p.calls[k], "pairs": p.pairs[k]}
         return out
 
     # --- geometry ------------------------------------------------------

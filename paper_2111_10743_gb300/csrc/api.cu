@@ -93,7 +93,7 @@ int lb_stage_out_finish(lb_ctx* c, void* dst, const void* dev, size_t bytes) {
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // profiling
-ProfScope::ProfScope(lb_ctx* ctx, int category) : c(ctx), cat(category) {
+ProfScope::ProfScope(lb_ctx* ctx, int category, int64_t npairs) : c(ctx), cat(category), pairs(npairs) {
   if (!c || !c->prof_on) return;
   if (c->ev_pool.empty()) {
     cudaEvent_t e;
@@ -115,7 +115,7 @@ ProfScope::~ProfScope() {
     c->ev_pool.pop_back();
   }
   cudaEventRecord(b, c->stream);
-  c->prof_pending.push_back({cat, a, b});
+  c->prof_pending.push_back({cat, a, b, pairs});
 }
 
 static int prof_resolve(lb_ctx* c) {
@@ -126,6 +126,7 @@ static int prof_resolve(lb_ctx* c) {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess && p.cat >= 0 && p.cat < LB_PROF_NCAT) {
       c->prof_ms[p.cat] += ms;
       c->prof_calls[p.cat] += 1;
+      c->prof_pairs[p.cat] += p.pairs;
     }
     c->ev_pool.push_back(p.a);
     c->ev_pool.push_back(p.b);
@@ -138,7 +139,7 @@ extern "C" int lb_set_profiling(lb_ctx* c, int on) {
   if (!c) return lb_fail(nullptr, LB_EINVAL, "null context");
   LB_CUDA(c, cudaSetDevice(c->device));
   LB_CHECK(prof_resolve(c));
-  for (int k = 0; k < LB_PROF_NCAT; ++k) { c->prof_ms[k] = 0; c->prof_calls[k] = 0; }
+  for (int k = 0; k < LB_PROF_NCAT; ++k) { c->prof_ms[k] = 0; c->prof_calls[k] = 0; c->prof_pairs[k] = 0; }
   c->launches = 0;
   c->prof_on = on ? 1 : 0;
   return LB_OK;
@@ -148,7 +149,11 @@ extern "C" int lb_get_profile(lb_ctx* c, lb_profile* out) {
   if (!c || !out) return lb_fail(c, LB_EINVAL, "null argument");
   LB_CUDA(c, cudaSetDevice(c->device));
   LB_CHECK(prof_resolve(c));
-  for (int k = 0; k < LB_PROF_NCAT; ++k) { out->ms[k] = c->prof_ms[k]; out->calls[k] = c->prof_calls[k]; }
+  for (int k = 0; k < LB_PROF_NCAT; ++k) {
+    out->ms[k] = c->prof_ms[k];
+    out->calls[k] = c->prof_calls[k];
+    out->pairs[k] = c->prof_pairs[k];
+  }
   out->launches = c->launches;
   return LB_OK;
 }
@@ -204,7 +209,7 @@ extern "C" int lb_create(lb_ctx** out, int device, const lb_params* p) {
     return lb_fail(nullptr, LB_ECUDA, "cudaSetDevice failed");
   }
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
-  if (cudaMallocHost((void**)&c->host_pinned, 64 * sizeof(double)) != cudaSuccess) {
+  if (cudaMallocHost((void**)&c->host_pinned, LB_PINNED_DOUBLES * sizeof(double)) != cudaSuccess) {
     delete c;
     return lb_fail(nullptr, LB_ENOMEM, "pinned host allocation failed");
   }
@@ -222,6 +227,7 @@ static void free_geometry(lb_ctx* c) {
 
 static void free_near(lb_ctx* c) {
   lb_free(&c->row_ptr); lb_free(&c->near_patch); lb_free(&c->vals);
+  lb_free(&c->vals_hi); lb_free(&c->vals_lo);
   for (auto& m : c->masks) lb_free(&m.flags);
   c->masks.clear();
   c->have_near = c->have_corr = false;
@@ -235,7 +241,7 @@ extern "C" int lb_destroy(lb_ctx* c) {
   free_geometry(c);
   free_near(c);
   for (DevBuf* b : {&c->ws_part, &c->ws_pot, &c->ws_src, &c->ws_vec, &c->ws_red, &c->ws_stage_in,
-                    &c->ws_stage_out, &c->ws_gm, &c->ws_quad})
+                    &c->ws_stage_out, &c->ws_gm, &c->ws_quad, &c->ws_bpot, &c->ws_bgm, &c->ws_bvec, &c->ws_dlow})
     if (b->p) cudaFree(b->p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   for (auto& p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -587,6 +593,8 @@ extern "C" int lb_load_corrections(lb_ctx* c, int64_t nnzb, const int64_t* row_p
   const int64_t N = c->N;
   LB_CHECK(lb_alloc(c, &c->row_ptr, N + 1));
   LB_CHECK(lb_alloc(c, &c->near_patch, nnzb));
+  lb_free(&c->vals_hi);
+  lb_free(&c->vals_lo);
   LB_CHECK(lb_alloc(c, &c->vals, nnzb * LB_NKERNELS * c->np));
   LB_CUDA(c, cudaMemcpyAsync(c->row_ptr, row_ptr, (N + 1) * sizeof(int64_t), cudaMemcpyDefault, c->stream));
   LB_CUDA(c, cudaMemcpyAsync(c->near_patch, patch, nnzb * sizeof(int32_t), cudaMemcpyDefault, c->stream));

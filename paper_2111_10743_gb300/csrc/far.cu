@@ -35,7 +35,9 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 template <typename R> struct V4T;
@@ -464,7 +466,7 @@ static int launch_far_t(lb_ctx* c, const void* srcA, const void* srcB, double* p
   const V4* tp = sizeof(R) == 4 ? (const V4*)c->pos32 : (const V4*)c->pos64;
   const V4* tn = sizeof(R) == 4 ? (const V4*)c->nrm32 : (const V4*)c->nrm64;
   dim3 grid((unsigned)ntb, (unsigned)nsplit);
-  ProfScope prof(c, (sizeof(R) == 4 ? LB_PROF_FAR32_K1 : LB_PROF_FAR64_K1) + KIND);
+  ProfScope prof(c, (sizeof(R) == 4 ? LB_PROF_FAR32_K1 : LB_PROF_FAR64_K1) + KIND, c->N * c->N);
   k_far<R, KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, c->np, tp, tn, (const V4*)srcA, (const V4*)srcB,
                                                           m->flags, ntiles, c->row_ptr, c->near_patch, tps, part);
   LB_LAUNCH(c);
@@ -485,7 +487,7 @@ static int launch_far32x2(lb_ctx* c, const void* srcA, const void* srcB, double*
   const int tps = (int)((ntiles + nsplit - 1) / nsplit);
   nsplit = (ntiles + tps - 1) / tps;
   dim3 grid((unsigned)ntb, (unsigned)nsplit);
-  ProfScope prof(c, LB_PROF_FAR32_K1 + KIND);
+  ProfScope prof(c, LB_PROF_FAR32_K1 + KIND, c->N * c->N);
   k_far32x2<KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, c->np, c->pos32, c->nrm32, (const float4*)srcA,
                                                             (const float4*)srcB, m->flags, ntiles, c->row_ptr,
                                                             c->near_patch, tps, part);
@@ -562,18 +564,36 @@ struct EpiSpec {
   int acc[4];            // accumulator index, or -1 for -(n_x . (a1, a2, a3)) (K1's S')
   double scale[4];       // multiplies the far accumulator
   int kern[4];           // correction kernel (LB_K_*), or -1 for none
-  const double* dens[4]; // density of the correction sum
+  const double* dens[4]; // density of the correction sum (float64)
+  const float* dh[4];    // its float32 copy / double-float hi part
+  const float* dl[4];    // its double-float lo part
   double* out[4];        // [N]
 };
 
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(F2 v) { return df_to_double(v); }
+
+// Split-partial reduction and near-field correction SpMV of one pass, one
+// warp per row.  The correction sums use the pass's own arithmetic: MODE 0
+// float64 (weights vals), MODE 1 float32 (weights vh, densities dh), MODE 2
+// double-float (weights vh + vl, densities dh + dl); float64 throughput on
+// GB300 is a small fraction of float32, and the float32 / double-float sums
+// match the accuracy of the pair sums they complete.
+template <int MODE>
 __global__ void k_epilogue(int64_t N, int np, int nsplit, int nacc, const double* __restrict__ part,
                            const double* __restrict__ nrm, const int64_t* __restrict__ row_ptr,
-                           const int32_t* __restrict__ near_patch, const double* __restrict__ vals, EpiSpec sp) {
+                           const int32_t* __restrict__ near_patch, const double* __restrict__ vals,
+                           const float* __restrict__ vh, const float* __restrict__ vl, EpiSpec sp) {
+  using T = typename std::conditional<MODE == 0, double, typename std::conditional<MODE == 1, float, F2>::type>::type;
   const int lane = threadIdx.x & 31;
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (i >= N) return;
-  double cs[4] = {0, 0, 0, 0};
-  if (vals) {
+  T cs[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) cs[o] = T{};
+  const bool corr = MODE == 0 ? vals != nullptr : vh != nullptr;
+  if (corr) {
     // the row's (block, node) pairs flattened; each lane walks them 32 apart,
     // four at a time so that their loads overlap, tracking (block, node)
     // incrementally instead of dividing
@@ -590,48 +610,111 @@ __global__ void k_epilogue(int64_t N, int np, int nsplit, int nacc, const double
         q += 32;
         while (q >= np) { q -= np; ++bo; }
       }
-      int64_t col[4];
-      const double* vb[4];
+      int64_t col[4], vo[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const bool ok = e + 32 * u < ne;
         const int64_t b = rb + (ok ? bl[u] : 0);
         col[u] = ok ? (int64_t)near_patch[b] * np + ql[u] : -1;
-        vb[u] = vals + b * stride + ql[u];
+        vo[u] = b * stride + ql[u];
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (col[u] < 0) continue;
 #pragma unroll
-        for (int o = 0; o < 4; ++o)
-          if (o < sp.nout && sp.kern[o] >= 0) cs[o] = fma(__ldg(vb[u] + sp.kern[o] * np), sp.dens[o][col[u]], cs[o]);
+        for (int o = 0; o < 4; ++o) {
+          if (o >= sp.nout || sp.kern[o] < 0) continue;
+          const int64_t w = vo[u] + sp.kern[o] * np;
+          if constexpr (MODE == 0)
+            cs[o] = fma(__ldg(vals + w), sp.dens[o][col[u]], cs[o]);
+          else if constexpr (MODE == 1)
+            cs[o] = fmaf(__ldg(vh + w), sp.dh[o][col[u]], cs[o]);
+          else
+            df_acc(cs[o], df_mul({__ldg(vh + w), __ldg(vl + w)}, {sp.dh[o][col[u]], sp.dl[o][col[u]]}));
+        }
       }
     }
-#pragma unroll
-    for (int o = 0; o < 4; ++o)
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) cs[o] += __shfl_xor_sync(0xffffffffu, cs[o], off);
+    warp_reduce_scatter<4>(cs, lane);  // lane 8 o holds output o
   }
-  if (lane != 0) return;
-  for (int o = 0; o < sp.nout; ++o) {
-    double f = 0;
-    if (sp.acc[o] >= 0) {
-      for (int s = 0; s < nsplit; ++s) f += part[((int64_t)s * nacc + sp.acc[o]) * N + i];
-    } else {
-      double g[3] = {0, 0, 0};
-      for (int s = 0; s < nsplit; ++s)
-        for (int k = 0; k < 3; ++k) g[k] += part[((int64_t)s * nacc + 1 + k) * N + i];
-      f = -(nrm[3 * i] * g[0] + nrm[3 * i + 1] * g[1] + nrm[3 * i + 2] * g[2]);
-    }
-    sp.out[o][i] = f * sp.scale[o] + cs[o];
+  const int o = lane >> 3;
+  if ((lane & 7) != 0 || o >= sp.nout) return;
+  double f = 0;
+  if (sp.acc[o] >= 0) {
+    for (int s = 0; s < nsplit; ++s) f += part[((int64_t)s * nacc + sp.acc[o]) * N + i];
+  } else {
+    double g[3] = {0, 0, 0};
+    for (int s = 0; s < nsplit; ++s)
+      for (int k = 0; k < 3; ++k) g[k] += part[((int64_t)s * nacc + 1 + k) * N + i];
+    f = -(nrm[3 * i] * g[0] + nrm[3 * i + 1] * g[1] + nrm[3 * i + 2] * g[2]);
+  }
+  sp.out[o][i] = f * sp.scale[o] + (corr ? to_d(cs[0]) : 0.0);
+}
+
+// hi = (float)x, lo = (float)(x - hi)
+__global__ void k_split_f64(int64_t n, const double* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float h = (float)v;
+    hi[i] = h;
+    if (lo) lo[i] = (float)(v - (double)h);
   }
 }
 
-static int run_epilogue(lb_ctx* c, int nsplit, int nacc, const double* part, const EpiSpec& sp) {
-  const int64_t threads = c->N * 32;
+int lb_split_f64(lb_ctx* c, int64_t n, const double* x, float* hi, float* lo) {
+  const unsigned nb = (unsigned)std::min<int64_t>(8LL * c->sm_count, std::max<int64_t>(1, lb_div_up(n, 256)));
+  k_split_f64<<<nb, 256, 0, c->stream>>>(n, x, hi, lo);
+  LB_LAUNCH(c);
+  return LB_OK;
+}
+
+// float32 hi / lo copies of the correction weights, made on first use after
+// the corrections were loaded or built
+int lb_lowp_vals(lb_ctx* c) {
+  if (!c->have_corr || c->vals_hi) return LB_OK;
+  const int64_t n = c->nnzb * LB_NKERNELS * c->np;
+  LB_CHECK(lb_alloc(c, &c->vals_hi, (size_t)n));
+  LB_CHECK(lb_alloc(c, &c->vals_lo, (size_t)n));
+  return lb_split_f64(c, n, c->vals, c->vals_hi, c->vals_lo);
+}
+
+// float32 / double-float copies of the distinct correction densities of sp
+static int lowp_dens(lb_ctx* c, int mode, EpiSpec& sp) {
+  const int64_t N = c->N;
+  LB_CHECK(lb_ensure(c, c->ws_dlow, (size_t)(8 * N) * sizeof(float)));
+  float* base = (float*)c->ws_dlow.p;
+  const double* uniq[4];
+  int nu = 0;
+  for (int o = 0; o < sp.nout; ++o) {
+    if (sp.kern[o] < 0) continue;
+    int j = 0;
+    while (j < nu && uniq[j] != sp.dens[o]) ++j;
+    if (j == nu) {
+      uniq[nu++] = sp.dens[o];
+      LB_CHECK(lb_split_f64(c, N, sp.dens[o], base + 2 * j * N, mode == 2 ? base + (2 * j + 1) * N : nullptr));
+    }
+    sp.dh[o] = base + 2 * j * N;
+    sp.dl[o] = base + (2 * j + 1) * N;
+  }
+  return LB_OK;
+}
+
+static int run_epilogue(lb_ctx* c, int prec, int nsplit, int nacc, const double* part, EpiSpec sp) {
+  const unsigned grid = lb_div_up(c->N * 32, 256);
+  const int mode = (!c->have_corr || prec == LB_FP64) ? 0 : (prec == LB_FP32 ? 1 : 2);
+  if (mode) {
+    LB_CHECK(lb_lowp_vals(c));
+    LB_CHECK(lowp_dens(c, mode, sp));
+  }
   ProfScope prof(c, LB_PROF_EPILOGUE);
-  k_epilogue<<<lb_div_up(threads, 256), 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr,
-                                                             c->near_patch, c->have_corr ? c->vals : nullptr, sp);
+  if (mode == 0)
+    k_epilogue<0><<<grid, 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr, c->near_patch,
+                                               c->have_corr ? c->vals : nullptr, nullptr, nullptr, sp);
+  else if (mode == 1)
+    k_epilogue<1><<<grid, 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr, c->near_patch,
+                                               nullptr, c->vals_hi, nullptr, sp);
+  else
+    k_epilogue<2><<<grid, 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr, c->near_patch,
+                                               nullptr, c->vals_hi, c->vals_lo, sp);
   LB_LAUNCH(c);
   return LB_OK;
 }
@@ -740,7 +823,7 @@ int lb_potentials(lb_ctx* c, int prec, const double* sigma, double* pot, unsigne
     ++o;
   }
   sp.nout = o;
-  return run_epilogue(c, nsplit, 4, part, sp);
+  return run_epilogue(c, prec, nsplit, 4, part, sp);
 }
 
 int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double* out) {
@@ -765,7 +848,7 @@ int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double*
     e1.nout = 2;
     e1.acc[0] = 0; e1.scale[0] = LB_INV4PI; e1.kern[0] = LB_K_S; e1.dens[0] = tau; e1.out[0] = mu + N;   // mu2
     e1.acc[1] = -1; e1.scale[1] = LB_INV4PI; e1.kern[1] = LB_K_SP; e1.dens[1] = tau; e1.out[1] = mu;     // mu1
-    LB_CHECK(run_epilogue(c, nsplit, 4, part, e1));
+    LB_CHECK(run_epilogue(c, prec, nsplit, 4, part, e1));
     // pass 2: charges mu1 (A.w), mu2 (B.w)
     LB_CHECK(pack_sources(c, prec, mu, mu + N, &A, &B));
     LB_CHECK(lb_far_launch(c, FAR_K2, prec, A, B, part, &nsplit));
@@ -775,7 +858,7 @@ int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double*
     e2.acc[1] = 1; e2.scale[1] = LB_INV4PI; e2.kern[1] = LB_K_S; e2.dens[1] = mu + N; e2.out[1] = pot + N;
     e2.acc[2] = 2; e2.scale[2] = -LB_INV4PI; e2.kern[2] = LB_K_SP; e2.dens[2] = mu + N; e2.out[2] = pot + 2 * N;
     e2.acc[3] = 3; e2.scale[3] = LB_INV4PI; e2.kern[3] = LB_K_SPPDP; e2.dens[3] = mu + N; e2.out[3] = pot + 3 * N;
-    LB_CHECK(run_epilogue(c, nsplit, 4, part, e2));
+    LB_CHECK(run_epilogue(c, prec, nsplit, 4, part, e2));
     k_wdot_partial<<<RED_BLOCKS, 256, 0, c->stream>>>(N, c->w, pot + N, partial);
     LB_LAUNCH(c);
     k_a3_final<<<nb, 256, 0, c->stream>>>(N, tau, pot, c->H, partial, RED_BLOCKS, c->area, out);
@@ -794,7 +877,7 @@ int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double*
     e1.dens[k] = tau;
     e1.out[k] = pot + (int64_t)k * N;
   }
-  LB_CHECK(run_epilogue(c, nsplit, 4, part, e1));
+  LB_CHECK(run_epilogue(c, prec, nsplit, 4, part, e1));
   k_wdot_partial<<<RED_BLOCKS, 256, 0, c->stream>>>(N, c->w, pot, partial);
   LB_LAUNCH(c);
   k_a2_mid<<<nb, 256, 0, c->stream>>>(N, pot, c->H, partial, RED_BLOCKS, c->area, mu + N);
@@ -806,7 +889,7 @@ int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double*
   e2.nout = 2;
   e2.acc[0] = 0; e2.scale[0] = LB_INV4PI; e2.kern[0] = LB_K_D; e2.dens[0] = pot + N; e2.out[0] = q;
   e2.acc[1] = 1; e2.scale[1] = LB_INV4PI; e2.kern[1] = LB_K_S; e2.dens[1] = mu + N; e2.out[1] = q + N;
-  LB_CHECK(run_epilogue(c, nsplit, 2, part, e2));
+  LB_CHECK(run_epilogue(c, prec, nsplit, 2, part, e2));
   k_a2_final<<<nb, 256, 0, c->stream>>>(N, tau, q, q + N, out);
   LB_LAUNCH(c);
   return LB_OK;
@@ -846,8 +929,8 @@ extern "C" int lb_far_sums(lb_ctx* c, int precision, int nrhs, const double* sig
       sp.kern[k] = -1;
       sp.out[k] = dout + ((int64_t)r * 4 + k) * N;
     }
-    k_epilogue<<<lb_div_up(N * 32, 256), 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr,
-                                                               c->near_patch, nullptr, sp);
+    k_epilogue<0><<<lb_div_up(N * 32, 256), 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr,
+                                                                  c->near_patch, nullptr, nullptr, nullptr, sp);
     LB_LAUNCH(c);
   }
   return lb_stage_out_finish(c, out, dout, nrhs * 4 * N * sizeof(double));
@@ -888,8 +971,14 @@ extern "C" int lb_apply_A(lb_ctx* c, int nrhs, const double* tau, double* out) {
   double* dout;
   LB_CHECK(lb_stage_in(c, tau, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
   LB_CHECK(lb_stage_out(c, out, nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dout));
-  for (int r = 0; r < nrhs; ++r)
-    LB_CHECK(lb_apply_op(c, c->params.formulation, pair_prec(c), din + r * N, dout + r * N));
+  const int prec = pair_prec(c);
+  if (c->params.formulation == LB_A3 && prec != LB_FP64 && nrhs >= 2) {
+    // several densities per far-field pass
+    LB_CHECK(lb_apply_a3_batch(c, prec, nrhs, din, dout, nullptr));
+  } else {
+    for (int r = 0; r < nrhs; ++r)
+      LB_CHECK(lb_apply_op(c, c->params.formulation, prec, din + r * N, dout + r * N));
+  }
   return lb_stage_out_finish(c, out, dout, nrhs * N * sizeof(double));
 }
 
@@ -1016,8 +1105,8 @@ extern "C" int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, cons
     sp.kern[k] = -1;
     sp.out[k] = out + (int64_t)k * N;
   }
-  k_epilogue<<<lb_div_up(N * 32, 256), 256, 0, st>>>(N, np, (int)nsplit, 4, part, nrm, row_ptr, near_patch,
-                                                     nullptr, sp);
+  k_epilogue<0><<<lb_div_up(N * 32, 256), 256, 0, st>>>(N, np, (int)nsplit, 4, part, nrm, row_ptr, near_patch,
+                                                        nullptr, nullptr, nullptr, sp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return lb_fail(nullptr, LB_ECUDA, "lb_far_sums_noalloc launch: %s", cudaGetErrorString(e));
   return LB_OK;

@@ -18,59 +18,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
-
-struct F2 {
-  float h, l;
-};
-
-__device__ __forceinline__ F2 two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
-// The pairs below are left unnormalised (no FastTwoSum after each
-// operation): hi + lo stays an exact-enough unevaluated sum with |lo| within a
-// few ulp of hi, and products drop only the lo * lo terms.
-__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
-  const F2 s = two_sum(a.h, b.h);
-  return {s.h, s.l + (a.l + b.l)};
-}
-__device__ __forceinline__ F2 df_sub(F2 a, F2 b) { return df_add(a, {-b.h, -b.l}); }
-__device__ __forceinline__ F2 df_mul(F2 a, F2 b) {
-  const float p = a.h * b.h;
-  return {p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)))};
-}
-__device__ __forceinline__ F2 df_sqr(F2 a) {
-  const float p = a.h * a.h;
-  return {p, fmaf(a.h + a.h, a.l, fmaf(a.h, a.h, -p))};
-}
-__device__ __forceinline__ F2 df_scale(F2 a, float s) {  // s a power of two or small integer
-  const float p = a.h * s;
-  return {p, fmaf(a.h, s, -p) + a.l * s};
-}
-// 1 / sqrt(x) with one Newton step on the float32 seed (one MUFU instruction)
-__device__ __forceinline__ F2 df_rsqrt(F2 x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x.h));
-  const float yy = y * y;
-  const F2 y2 = {yy, fmaf(y, y, -yy)};
-  const F2 xy2 = df_mul(x, y2);
-  const float e = (1.f - xy2.h) - xy2.l;
-  return fast_two_sum(y, 0.5f * y * e);
-}
-__device__ __forceinline__ void df_acc(F2& acc, F2 t) {
-  const F2 s = two_sum(acc.h, t.h);
-  acc.h = s.h;
-  acc.l += s.l + t.l;
-}
-__device__ __forceinline__ F2 df_dot3(F2 a0, F2 a1, F2 a2, F2 b0, F2 b1, F2 b2) {
-  return df_add(df_add(df_mul(a0, b0), df_mul(a1, b1)), df_mul(a2, b2));
-}
 
 template <int KIND> struct DfOut { static const int n = 4; };
 template <> struct DfOut<FAR_K4> { static const int n = 2; };
@@ -262,7 +211,7 @@ static int launch_df_t(lb_ctx* c, const void* S, double* part, int* nsplit_out) 
   const int tps = (int)((ntiles + nsplit - 1) / nsplit);
   nsplit = (ntiles + tps - 1) / tps;
   dim3 grid((unsigned)ntb, (unsigned)nsplit);
-  ProfScope prof(c, LB_PROF_FARDF_K1 + KIND);
+  ProfScope prof(c, LB_PROF_FARDF_K1 + KIND, c->N * c->N);
   k_far_df<KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, c->np, (const float4*)S, m->flags, ntiles,
                                                            c->row_ptr, c->near_patch, tps, c->Npad, part);
   LB_LAUNCH(c);

@@ -13,6 +13,8 @@
 
 #define LB_PI 3.14159265358979323846
 #define LB_INV4PI (1.0 / (4.0 * LB_PI))
+#define LB_PINNED_DOUBLES 1024
+#define LB_BATCH_MAX 64  // right-hand sides advanced in lockstep by one batched solve
 
 // Device buffer owned by a context; grows on demand and never shrinks.
 struct DevBuf {
@@ -38,6 +40,7 @@ struct MaskTable {
 struct ProfPending {
   int cat;
   cudaEvent_t a, b;
+  int64_t pairs;
 };
 
 struct lb_ctx {
@@ -85,6 +88,8 @@ struct lb_ctx {
   int64_t* row_ptr = nullptr;   // [N+1]
   int32_t* near_patch = nullptr;  // [nnzb]
   double* vals = nullptr;       // [nnzb][4][np]
+  float* vals_hi = nullptr;     // [nnzb][4][np] float32 copy (double-float hi part), made on first use
+  float* vals_lo = nullptr;     // [nnzb][4][np] double-float lo part
   std::vector<MaskTable> masks;
 
   // profiling
@@ -94,10 +99,13 @@ struct lb_ctx {
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[LB_PROF_NCAT] = {0};
   int64_t prof_calls[LB_PROF_NCAT] = {0};
+  int64_t prof_pairs[LB_PROF_NCAT] = {0};
 
   // workspace
   DevBuf ws_part, ws_pot, ws_src, ws_vec, ws_red, ws_stage_in, ws_stage_out, ws_gm, ws_quad;
-  double* host_pinned = nullptr;  // small pinned scalars for GMRES control
+  DevBuf ws_bpot, ws_bgm, ws_bvec;  // batched applies and the lockstep solver
+  DevBuf ws_dlow;                   // float32 / double-float copies of correction densities
+  double* host_pinned = nullptr;  // pinned scalars for GMRES control [LB_PINNED_DOUBLES]
 };
 
 // ---- error handling --------------------------------------------------------
@@ -121,12 +129,14 @@ int lb_fail(lb_ctx* c, int code, const char* fmt, ...);
   } while (0)
 
 // Times the launches enqueued during its lifetime under category `cat` when
-// profiling is on (two events recorded on the context stream).
+// profiling is on (two events recorded on the context stream); `pairs` is the
+// number of (target, source, density) pair evaluations they make.
 struct ProfScope {
   lb_ctx* c;
   int cat;
+  int64_t pairs;
   cudaEvent_t a = nullptr;
-  ProfScope(lb_ctx* ctx, int category);
+  ProfScope(lb_ctx* ctx, int category, int64_t npairs = 0);
   ~ProfScope();
 };
 
@@ -168,8 +178,17 @@ int lb_potentials(lb_ctx* c, int prec, const double* sigma, double* pot, unsigne
 // apply the formulation operator to one vector (device in, device out)
 int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double* out);
 int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out);
+// float32 hi / lo copies of the correction weights (no-op when present)
+int lb_lowp_vals(lb_ctx* c);
+// hi[i] = (float)x[i], lo[i] = (float)(x[i] - hi[i]) (lo may be null)
+int lb_split_f64(lb_ctx* c, int64_t n, const double* x, float* hi, float* lo);
 int lb_pack_df(lb_ctx* c, const double* d1, const double* d2, void* S);
 int lb_far_launch_df(lb_ctx* c, int kind, const void* S, double* part, int* nsplit);
+// A3 applied to R densities tau[R][N] -> out[R][N] with several densities per
+// far-field pass (prec LB_FP32 or LB_DF64); u (may be null) receives S[S[tau]]
+int lb_apply_a3_batch(lb_ctx* c, int prec, int R, const double* tau, double* out, double* u);
+// S applied to R densities sig[R][N] -> out[R][N] (far + near)
+int lb_apply_s_batch(lb_ctx* c, int prec, int R, const double* sig, double* out);
 // weighted mean of a device vector (deterministic), result to host
 int lb_wmean(lb_ctx* c, const double* f, double* mean_host);
 // counters of the last solve

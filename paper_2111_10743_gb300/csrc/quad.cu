@@ -356,6 +356,8 @@ extern "C" int lb_build_corrections(lb_ctx* c) {
         leb = std::max(leb, sum);
       }
   }
+  lb_free(&c->vals_hi);
+  lb_free(&c->vals_lo);
   LB_CHECK(lb_alloc(c, &c->vals, (size_t)c->nnzb * LB_NKERNELS * np));
   LB_CHECK(lb_ensure(c, c->ws_quad, (size_t)(3 * c->npatch * np + 16) * sizeof(double)));
   double* cX = (double*)c->ws_quad.p;

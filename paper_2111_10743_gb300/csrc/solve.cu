@@ -151,6 +151,7 @@ __global__ void k_check_finite(int64_t N, const double* __restrict__ x, int* __r
 // ---------------------------------------------------------------------------
 struct Gm {
   int m, ldh;
+  int64_t ldv;  // distance between consecutive basis vectors of this system
   double *V, *h, *Hm, *cs, *sn, *g, *y, *partial, *scal, *w;
 };
 
@@ -163,6 +164,7 @@ static int gm_work(lb_ctx* c, int m, Gm* G) {
   double* p = (double*)c->ws_gm.p;
   G->m = m;
   G->ldh = ldh;
+  G->ldv = N;
   G->V = p; p += (size_t)(m + 1) * N;
   G->h = p; p += m + 2;
   G->Hm = p; p += (size_t)ldh * m;
@@ -180,7 +182,7 @@ static unsigned vec_blocks(lb_ctx* c) { return (unsigned)std::min<int64_t>(4 * c
 
 // squared norm / dots into dst (device) via fixed-order partials
 static int dots(lb_ctx* c, Gm& G, int nvec, const double* V, const double* w, double* dst, int accumulate) {
-  k_multidot<<<GM_RB, 256, 0, c->stream>>>(c->N, nvec, V, c->N, w, G.partial);
+  k_multidot<<<GM_RB, 256, 0, c->stream>>>(c->N, nvec, V, G.ldv, w, G.partial);
   LB_LAUNCH(c);
   k_reduce_cols<<<lb_div_up(nvec, 64), 64, 0, c->stream>>>(nvec, GM_RB, G.partial, dst, accumulate);
   LB_LAUNCH(c);
@@ -191,6 +193,31 @@ static int read_scalar(lb_ctx* c, const double* d, double* h) {
   LB_CUDA(c, cudaMemcpyAsync(c->host_pinned, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   LB_CUDA(c, cudaStreamSynchronize(c->stream));
   *h = c->host_pinned[0];
+  return LB_OK;
+}
+
+// After w = A v_j: classical Gram-Schmidt twice (h = V^T w, w -= V h,
+// h2 = V^T w, w -= V h2, h += h2), v_{j+1} = w / |w|, and the Givens update
+// of column j; G.scal[0] then holds the residual estimate.
+static int arnoldi_step(lb_ctx* c, Gm& G, int j, double beta) {
+  const int64_t N = c->N;
+  const unsigned nb = vec_blocks(c);
+  double* vn = G.V + (int64_t)(j + 1) * G.ldv;
+  LB_CHECK(dots(c, G, j + 1, G.V, G.w, G.h, 0));
+  k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, j + 1, G.V, G.ldv, G.h, G.w);
+  LB_LAUNCH(c);
+  LB_CHECK(dots(c, G, j + 1, G.V, G.w, G.y, 0));
+  k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, j + 1, G.V, G.ldv, G.y, G.w);
+  LB_LAUNCH(c);
+  k_add_small<<<lb_div_up(j + 1, 128), 128, 0, c->stream>>>(j + 1, G.y, G.h);
+  LB_LAUNCH(c);
+  LB_CHECK(dots(c, G, 1, G.w, G.w, G.scal + 2, 0));
+  k_sqrt_to<<<1, 32, 0, c->stream>>>(G.scal + 2, G.h + j + 1);
+  LB_LAUNCH(c);
+  k_scale_by<<<nb, 256, 0, c->stream>>>(N, G.w, G.h + j + 1, vn);
+  LB_LAUNCH(c);
+  k_givens<<<1, 32, 0, c->stream>>>(j, G.ldh, G.h, G.Hm, G.cs, G.sn, G.g, beta, G.scal);
+  LB_LAUNCH(c);
   return LB_OK;
 }
 
@@ -226,24 +253,8 @@ static int gmres(lb_ctx* c, int prec, const double* b, double* x, double tol, in
   double r = 1.0;
   for (int j = 0; j < max_iter; ++j) {
     const double* vj = G.V + (int64_t)j * N;
-    double* vn = G.V + (int64_t)(j + 1) * N;
     LB_CHECK(lb_apply_op(c, c->params.formulation, prec, vj, G.w));
-    // classical Gram-Schmidt, twice: h = V^T w, w -= V h, h2 = V^T w, w -= V h2, h += h2
-    LB_CHECK(dots(c, G, j + 1, G.V, G.w, G.h, 0));
-    k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, j + 1, G.V, N, G.h, G.w);
-    LB_LAUNCH(c);
-    LB_CHECK(dots(c, G, j + 1, G.V, G.w, G.y, 0));
-    k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, j + 1, G.V, N, G.y, G.w);
-    LB_LAUNCH(c);
-    k_add_small<<<lb_div_up(j + 1, 128), 128, 0, c->stream>>>(j + 1, G.y, G.h);
-    LB_LAUNCH(c);
-    LB_CHECK(dots(c, G, 1, G.w, G.w, G.scal + 2, 0));
-    k_sqrt_to<<<1, 32, 0, c->stream>>>(G.scal + 2, G.h + j + 1);
-    LB_LAUNCH(c);
-    k_scale_by<<<nb, 256, 0, c->stream>>>(N, G.w, G.h + j + 1, vn);
-    LB_LAUNCH(c);
-    k_givens<<<1, 32, 0, c->stream>>>(j, G.ldh, G.h, G.Hm, G.cs, G.sn, G.g, beta, G.scal);
-    LB_LAUNCH(c);
+    LB_CHECK(arnoldi_step(c, G, j, beta));
     LB_CHECK(read_scalar(c, G.scal, &r));
     if (hist) hist->push_back(r);
     k = j + 1;
@@ -386,6 +397,275 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
   return LB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Lockstep solves of R right-hand sides (A3, float32 or double-float pairs).
+//
+// The R systems advance together: each GMRES iteration applies A3 once to
+// the current basis vectors of all systems still iterating (one batched
+// far-field pass per A3 pass, several densities per pair evaluation), then
+// runs the Arnoldi step of each system.  The j-th basis vectors of all
+// systems are adjacent ([m+1][R][N]), so with every system active the batched
+// apply reads them in place; once some have converged, the active ones are
+// gathered first.  A system stops when its own residual estimate is below
+// tol, exactly as it would alone.
+struct Lockstep {
+  int R = 0, m = 0;
+  double* V = nullptr;   // [m+1][R][N]
+  double* in = nullptr;  // [R][N] gathered apply input
+  double* out = nullptr; // [R][N] apply output
+  std::vector<Gm> G;
+};
+
+static int lockstep_work(lb_ctx* c, int R, int m, Lockstep* L) {
+  const int64_t N = c->N;
+  const int ldh = m + 1;
+  const size_t small = (size_t)(m + 2) * 5 + (size_t)ldh * m + 8;
+  const size_t need = (size_t)(m + 1) * R * N + 2 * (size_t)R * N + (size_t)GM_RB * (m + 2) + small * R;
+  LB_CHECK(lb_ensure(c, c->ws_bgm, need * sizeof(double)));
+  double* p = (double*)c->ws_bgm.p;
+  L->R = R;
+  L->m = m;
+  L->V = p; p += (size_t)(m + 1) * R * N;
+  L->in = p; p += (size_t)R * N;
+  L->out = p; p += (size_t)R * N;
+  double* partial = p; p += (size_t)GM_RB * (m + 2);
+  L->G.assign(R, Gm{});
+  for (int r = 0; r < R; ++r) {
+    Gm& G = L->G[r];
+    G.m = m;
+    G.ldh = ldh;
+    G.ldv = (int64_t)R * N;
+    G.V = L->V + (int64_t)r * N;
+    G.partial = partial;
+    G.h = p; p += m + 2;
+    G.Hm = p; p += (size_t)ldh * m;
+    G.cs = p; p += m + 2;
+    G.sn = p; p += m + 2;
+    G.g = p; p += m + 2;
+    G.y = p; p += m + 2;
+    G.scal = p; p += 8;
+    G.w = nullptr;
+  }
+  return LB_OK;
+}
+
+// device scalars d[k] (one per listed system) -> host, one synchronisation
+static int read_scalars(lb_ctx* c, const std::vector<const double*>& d, std::vector<double>* h) {
+  if ((int)d.size() > LB_PINNED_DOUBLES) return lb_fail(c, LB_EINVAL, "too many systems in one readback");
+  for (size_t k = 0; k < d.size(); ++k)
+    LB_CUDA(c, cudaMemcpyAsync(c->host_pinned + k, d[k], sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  h->assign(c->host_pinned, c->host_pinned + d.size());
+  return LB_OK;
+}
+
+// |v_r| for the listed systems of v [R][N]
+static int norms_of(lb_ctx* c, Lockstep& L, const double* v, const std::vector<int>& sys, std::vector<double>* out) {
+  std::vector<const double*> d;
+  for (int r : sys) {
+    Gm& G = L.G[r];
+    const double* vr = v + (int64_t)r * c->N;
+    LB_CHECK(dots(c, G, 1, vr, vr, G.scal + 4, 0));
+    d.push_back(G.scal + 4);
+  }
+  LB_CHECK(read_scalars(c, d, out));
+  for (double& x : *out) x = sqrt(x);
+  return LB_OK;
+}
+
+// dst[a] = src[sys[a]] (rows of N doubles)
+static int gather_rows(lb_ctx* c, const double* src, const std::vector<int>& sys, double* dst) {
+  for (size_t a = 0; a < sys.size(); ++a)
+    LB_CUDA(c, cudaMemcpyAsync(dst + (int64_t)a * c->N, src + (int64_t)sys[a] * c->N, c->N * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->stream));
+  return LB_OK;
+}
+
+// GMRES on R systems at once: b, x [R][N]; systems with b = 0 get x = 0
+static int gmres_lockstep(lb_ctx* c, Lockstep& L, int prec, const double* b, double* x, double tol, int max_iter,
+                          std::vector<int>* its, std::vector<double>* res, std::vector<double>* hist0) {
+  const int64_t N = c->N;
+  const int R = L.R;
+  const unsigned nb = vec_blocks(c);
+  its->assign(R, 0);
+  res->assign(R, 0.0);
+  std::vector<int> all(R);
+  for (int r = 0; r < R; ++r) all[r] = r;
+  std::vector<double> beta;
+  LB_CHECK(norms_of(c, L, b, all, &beta));
+  std::vector<int> act;
+  for (int r = 0; r < R; ++r) {
+    if (!std::isfinite(beta[r])) return lb_fail(c, LB_EINVAL, "non-finite right-hand side");
+    Gm& G = L.G[r];
+    if (!(beta[r] > 0)) {
+      LB_CUDA(c, cudaMemsetAsync(x + (int64_t)r * N, 0, N * sizeof(double), c->stream));
+      continue;
+    }
+    act.push_back(r);
+    LB_CUDA(c, cudaMemsetAsync(G.g, 0, (G.m + 2) * sizeof(double), c->stream));
+    k_sqrt_to<<<1, 32, 0, c->stream>>>(G.scal + 4, G.g);
+    LB_LAUNCH(c);
+    k_scale_by<<<nb, 256, 0, c->stream>>>(N, b + (int64_t)r * N, G.g, G.V);
+    LB_LAUNCH(c);
+  }
+  if (hist0 && R > 0 && beta[0] > 0) hist0->push_back(1.0);
+  for (int j = 0; j < max_iter && !act.empty(); ++j) {
+    const int Ra = (int)act.size();
+    const double* Vj = L.V + (int64_t)j * R * N;
+    const double* in = Vj;
+    if (Ra < R) {
+      for (int a = 0; a < Ra; ++a)
+        LB_CUDA(c, cudaMemcpyAsync(L.in + (int64_t)a * N, Vj + (int64_t)act[a] * N, N * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, c->stream));
+      in = L.in;
+    }
+    LB_CHECK(lb_apply_a3_batch(c, prec, Ra, in, L.out, nullptr));
+    std::vector<const double*> d;
+    for (int a = 0; a < Ra; ++a) {
+      Gm& G = L.G[act[a]];
+      G.w = L.out + (int64_t)a * N;
+      LB_CHECK(arnoldi_step(c, G, j, beta[act[a]]));
+      d.push_back(G.scal);
+    }
+    std::vector<double> rr;
+    LB_CHECK(read_scalars(c, d, &rr));
+    std::vector<int> next;
+    for (int a = 0; a < Ra; ++a) {
+      const int r = act[a];
+      if (!std::isfinite(rr[a])) return lb_fail(c, LB_EINVAL, "GMRES breakdown: non-finite residual");
+      (*its)[r] = j + 1;
+      (*res)[r] = rr[a];
+      if (hist0 && r == 0) hist0->push_back(rr[a]);
+      if (!(rr[a] < tol || rr[a] == 0.0)) next.push_back(r);
+    }
+    act.swap(next);
+  }
+  for (int r = 0; r < R; ++r) {
+    if (!(beta[r] > 0)) continue;
+    Gm& G = L.G[r];
+    k_backsolve<<<1, 32, 0, c->stream>>>((*its)[r], G.ldh, G.Hm, G.g, G.y);
+    LB_LAUNCH(c);
+    k_combine<<<nb, 256, 0, c->stream>>>(N, (*its)[r], G.V, G.ldv, G.y, x + (int64_t)r * N, 0);
+    LB_LAUNCH(c);
+  }
+  return LB_OK;
+}
+
+// R mean-zero right-hand sides b [R][N] -> densities sigma and potentials u
+// (A3, u = S[S[sigma]]), precision LB_FP32, LB_DF64 or LB_FP32_REFINED.
+static int solve_lockstep(lb_ctx* c, int R, const double* b, double* sigma, double* u, lb_solve_info* info,
+                          bool first) {
+  const int64_t N = c->N;
+  const lb_params& p = c->params;
+  const unsigned nb = vec_blocks(c);
+  const int64_t RN = (int64_t)R * N;
+  Lockstep L;
+  LB_CHECK(lockstep_work(c, R, p.max_iter, &L));
+  LB_CHECK(lb_ensure(c, c->ws_bvec, (size_t)(7 * RN) * sizeof(double)));
+  double* r = (double*)c->ws_bvec.p;  // residuals [R][N]
+  double* delta = r + RN;             // corrections (gathered) [Ra][N]
+  double* Ax = delta + RN;            // apply output (gathered)
+  double* x1 = Ax + RN;               // first iterates
+  double* ux1 = x1 + RN;              // their double-float potentials S[S[x1]]
+  double* tmp = ux1 + RN;
+  double* rin = tmp + RN;             // gathered residuals
+  std::vector<double> hist;
+  std::vector<int> its;
+  std::vector<double> res;
+  if (p.precision != LB_FP32_REFINED) {
+    LB_CHECK(gmres_lockstep(c, L, p.precision, b, sigma, p.tol, p.max_iter, &its, &res, &hist));
+    for (int k = 0; k < R; ++k) {
+      info->iterations += its[k];
+      info->converged = info->converged && (res[k] < p.tol);
+      info->rel_residual = std::max(info->rel_residual, res[k]);
+    }
+    // u = S[S[sigma]] in the solve's own pair arithmetic
+    LB_CHECK(lb_apply_s_batch(c, p.precision, R, sigma, tmp));
+    LB_CHECK(lb_apply_s_batch(c, p.precision, R, tmp, u));
+  } else {
+    std::vector<int> all(R);
+    for (int k = 0; k < R; ++k) all[k] = k;
+    std::vector<double> nbv;
+    LB_CHECK(norms_of(c, L, b, all, &nbv));
+    LB_CUDA(c, cudaMemsetAsync(sigma, 0, RN * sizeof(double), c->stream));
+    LB_CUDA(c, cudaMemsetAsync(x1, 0, RN * sizeof(double), c->stream));
+    LB_CUDA(c, cudaMemsetAsync(ux1, 0, RN * sizeof(double), c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(r, b, RN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    std::vector<int> act;
+    std::vector<double> rel(R, 0.0);
+    std::vector<int> steps(R, 0), itsum(R, 0);
+    for (int k = 0; k < R; ++k) {
+      if (nbv[k] != 0.0) { act.push_back(k); rel[k] = 1.0; }
+    }
+    if (R > 0 && nbv[0] != 0.0) hist.push_back(1.0);
+    for (int s = 0; s < p.max_refine && !act.empty(); ++s) {
+      const int Ra = (int)act.size();
+      LB_CHECK(gather_rows(c, r, act, rin));
+      Lockstep La;
+      LB_CHECK(lockstep_work(c, Ra, p.max_iter, &La));
+      LB_CHECK(gmres_lockstep(c, La, LB_FP32, rin, delta, p.inner_tol, p.max_iter, &its, &res, nullptr));
+      for (int a = 0; a < Ra; ++a) {
+        itsum[act[a]] += its[a];
+        k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, delta + (int64_t)a * N, 1.0, sigma + (int64_t)act[a] * N);
+        LB_LAUNCH(c);
+      }
+      if (s == 0) {
+        // r = b - A x1 in double-float; keep x1 and S[S[x1]]
+        LB_CHECK(gather_rows(c, sigma, act, rin));
+        LB_CHECK(lb_apply_a3_batch(c, LB_DF64, Ra, rin, Ax, tmp));
+        for (int a = 0; a < Ra; ++a) {
+          const int64_t o = (int64_t)act[a] * N;
+          LB_CUDA(c, cudaMemcpyAsync(ux1 + o, tmp + (int64_t)a * N, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                     c->stream));
+          LB_CUDA(c, cudaMemcpyAsync(x1 + o, sigma + o, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+          LB_CUDA(c, cudaMemcpyAsync(r + o, b + o, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+          k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, Ax + (int64_t)a * N, 1.0, r + o);
+          LB_LAUNCH(c);
+        }
+      } else {
+        // r -= A32 delta: delta is about inner_tol |x|, so float32 pairs keep
+        // this update accurate to about 1e-7 inner_tol |b|
+        LB_CHECK(lb_apply_a3_batch(c, LB_FP32, Ra, delta, Ax, nullptr));
+        for (int a = 0; a < Ra; ++a) {
+          k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, Ax + (int64_t)a * N, 1.0, r + (int64_t)act[a] * N);
+          LB_LAUNCH(c);
+        }
+      }
+      std::vector<double> rn;
+      LB_CHECK(norms_of(c, L, r, act, &rn));
+      std::vector<int> next;
+      for (int a = 0; a < Ra; ++a) {
+        const int k = act[a];
+        rel[k] = rn[a] / nbv[k];
+        ++steps[k];
+        if (k == 0) hist.push_back(rel[k]);
+        if (!(rel[k] < p.tol)) next.push_back(k);
+      }
+      act.swap(next);
+    }
+    for (int k = 0; k < R; ++k) {
+      info->iterations += itsum[k];
+      info->refinements += steps[k];
+      info->converged = info->converged && (rel[k] < p.tol);
+      info->rel_residual = std::max(info->rel_residual, rel[k]);
+    }
+    // u = S[S[x1]] (double-float) + float32 potential of x - x1
+    LB_CUDA(c, cudaMemcpyAsync(tmp, sigma, RN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    k_axpby<<<nb, 256, 0, c->stream>>>(RN, -1.0, x1, 1.0, tmp);
+    LB_LAUNCH(c);
+    LB_CHECK(lb_apply_s_batch(c, LB_FP32, R, tmp, Ax));
+    LB_CHECK(lb_apply_s_batch(c, LB_FP32, R, Ax, tmp));
+    LB_CUDA(c, cudaMemcpyAsync(u, ux1, RN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    k_axpby<<<nb, 256, 0, c->stream>>>(RN, 1.0, tmp, 1.0, u);
+    LB_LAUNCH(c);
+  }
+  if (first) {
+    info->history_len = (int32_t)std::min<size_t>(hist.size(), 128);
+    for (int i = 0; i < info->history_len; ++i) info->history[i] = hist[i];
+  }
+  return LB_OK;
+}
+
 static int solve_batch(lb_ctx* c, int nrhs, const double* f, double* u, lb_solve_info* info) {
   const int64_t N = c->N;
   const lb_params& p = c->params;
@@ -396,11 +676,44 @@ static int solve_batch(lb_ctx* c, int nrhs, const double* f, double* u, lb_solve
   double* tmp = fb + 8 * N;
   // solution potentials of the plain modes in their own pair arithmetic
   const int post = p.precision == LB_FP32 ? LB_FP32 : (p.precision == LB_FP64 ? LB_FP64 : LB_DF64);
+  // the finite-check flag lives in ws_red, which later applies may grow:
+  // its address is taken afresh before every use
+  auto bad_flag = [&](int** d) {
+    LB_CHECK(lb_ensure(c, c->ws_red, 8192));
+    *d = (int*)((char*)c->ws_red.p + 8192 - 64);
+    return LB_OK;
+  };
   int* dbad = nullptr;
-  LB_CHECK(lb_ensure(c, c->ws_red, 4096));
-  dbad = (int*)((char*)c->ws_red.p + 3072);
+  if (p.formulation == LB_A3 && p.precision != LB_FP64 && nrhs >= 2) {
+    // several right-hand sides in lockstep, in groups of LB_BATCH_MAX
+    lb_solve_info local{};
+    if (!info) { local.converged = 1; info = &local; }
+    for (int r0 = 0; r0 < nrhs; r0 += LB_BATCH_MAX) {
+      const int R = std::min(LB_BATCH_MAX, nrhs - r0);
+      LB_CHECK(lb_ensure(c, c->ws_quad, (size_t)(2 * R * N) * sizeof(double)));
+      double* bg = (double*)c->ws_quad.p;
+      double* sg = bg + (int64_t)R * N;
+      for (int k = 0; k < R; ++k) {
+        const double* fr = f + (int64_t)(r0 + k) * N;
+        LB_CHECK(bad_flag(&dbad));
+        LB_CUDA(c, cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
+        k_check_finite<<<vec_blocks(c), 256, 0, c->stream>>>(N, fr, dbad);
+        LB_LAUNCH(c);
+        int bad = 0;
+        LB_CUDA(c, cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LB_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (bad) return lb_fail(c, LB_EINVAL, "right-hand side %d has non-finite entries", r0 + k);
+        double removed = 0;
+        LB_CHECK(project_mean_zero(c, fr, bg + (int64_t)k * N, &removed));
+        if (r0 + k == 0) info->removed_mean = removed;
+      }
+      LB_CHECK(solve_lockstep(c, R, bg, sg, u + (int64_t)r0 * N, info, r0 == 0));
+    }
+    return LB_OK;
+  }
   for (int r = 0; r < nrhs; ++r) {
     const double* fr = f + (int64_t)r * N;
+    LB_CHECK(bad_flag(&dbad));
     LB_CUDA(c, cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
     k_check_finite<<<vec_blocks(c), 256, 0, c->stream>>>(N, fr, dbad);
     LB_LAUNCH(c);
