@@ -45,9 +45,9 @@ if ROOT not in sys.path:
 
 METRIC = "Layer-potential apply Ginteractions/s; time-to-solve at 1e-10 rel. residual"
 UNIT = "Ginteractions/s"
-WORKLOAD = ("ellipsoid (1,1.5,2), 1280 order-8 patches (N=57,600), f = 8 Gaussian bumps; "
+WORKLOAD = ("ellipsoid (1,1.5,2), {P} order-8 patches (N={N:,}), f = 8 Gaussian bumps; "
             "A3 solve to 1e-10 rel. residual")
-WORKLOAD_TORUS = ("torus R=2 r=0.75, 2048 order-6 patches (N=57,344), batch of 18 RHS: 16 random Legendre f "
+WORKLOAD_TORUS = ("torus R=2 r=0.75, {P} order-6 patches (N={N:,}), batch of 18 RHS: 16 random Legendre f "
                   "+ the 2 Hodge RHS div F, -div(n x F); A3 lockstep solve to 1e-10 rel. residual")
 
 # far-field flops per evaluated pair, counting an FMA as two (kernel source in
@@ -166,6 +166,9 @@ def run_ours(args):
         w = ellipsoid_gauss(2, 8, 1002)
     elif args.case == "torus_batch":
         w = config(3)
+    elif args.case == "torus_small":   # the batch on a 16 x 16 torus (N = 14,336), for profiler captures
+        from workloads.configs import torus_batch
+        w = torus_batch(16, 16, 6, 16, 1003)
     else:
         w = config(2)
     s = w.surface
@@ -180,7 +183,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_q = time.time() - t0
     fb = w.f
-    if args.case == "torus_batch":   # right-hand sides of the two Hodge potentials (Section 5)
+    if args.case in ("torus_batch", "torus_small"):   # right-hand sides of the two Hodge potentials (Section 5)
         n, _, _ = ctx.get_geometry()
         F = w.extra["F"]
         fb = np.concatenate([w.f, ctx.surface_div(F[None]), -ctx.surface_div(np.cross(n, F)[None])])
@@ -286,7 +289,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp32_refined": "f32 + double-float pairs, f64 solve", "fp64": "f64",
                   "fp32": "f32 pairs, f64 solve"}[args.precision],
         "data": "synthetic", "time_to_solve_ms": round(ms_step, 3), "t_q_s": round(t_q, 2),
-        "config": {"workload": WORKLOAD_TORUS if args.case == "torus_batch" else WORKLOAD, "N": s.N,
+        "config": {"workload": (WORKLOAD_TORUS if args.case.startswith("torus") else WORKLOAD).format(
+                       P=s.npatch, N=s.N), "N": s.N,
                    "patches": s.npatch, "order": s.order, "nrhs": int(nrhs),
                    "formulation": "A3", "precision": args.precision, "tol": 1e-10, "eps_quad": 1e-12,
                    "near_factor": 2.0, "l2": "512 MB write between timed steps",
@@ -302,7 +306,7 @@ def run_ours(args):
         "gpu_launches": int(prof["launches"]),
         "clocks": clocks,
     }
-    if ws == 1 and not args.no_cpu_baseline and args.case != "torus_batch":
+    if ws == 1 and not args.no_cpu_baseline and not args.case.startswith("torus"):
         out["cpu_baseline"] = cpu_baseline(args.cpu_targets)
     print(json.dumps(out))
 
@@ -368,7 +372,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": geo.N, "sample_targets": args.cpu_targets},
+        "config": {"workload": WORKLOAD.format(P=geo.N // 45, N=geo.N), "N": geo.N,
+                   "sample_targets": args.cpu_targets},
         "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"A3 apply far sums for {args.cpu_targets} sampled targets x {geo.N} sources"},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -384,9 +389,10 @@ def main():
     ap.add_argument("--precision", default="fp32_refined", choices=["fp32_refined", "fp64", "fp32"])
     ap.add_argument("--cpu-targets", type=int, default=0, help="oracle sample size (0: every target)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="full", choices=["full", "small", "torus_batch"],
+    ap.add_argument("--case", default="full", choices=["full", "small", "torus_batch", "torus_small"],
                     help="full: the benchmark surface; small: 320 patches of the same kind (profiling); "
-                         "torus_batch: the torus with 18 right-hand sides solved in lockstep")
+                         "torus_batch: the torus with 18 right-hand sides solved in lockstep; "
+                         "torus_small: the same batch on a 16 x 16 torus (profiling)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -63,6 +63,25 @@ __device__ __forceinline__ F2 df_dot3(F2 a0, F2 a1, F2 a2, F2 b0, F2 b1, F2 b2) 
 }
 __device__ __forceinline__ double df_to_double(F2 a) { return (double)a.h + (double)a.l; }
 
+// ---- packed float32 pairs ---------------------------------------------------
+// sm_100-family f32x2 instructions: one instruction on two floats held in a
+// 64-bit register (the first operand of pk2 in the low half)
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk2(float a, float b) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(u64 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ u64 add2(u64 a, u64 b) { u64 r; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) { u64 r; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) { u64 r; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 // ---- warp reductions --------------------------------------------------------
 __device__ __forceinline__ float shfl_xor_v(float v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
 __device__ __forceinline__ double shfl_xor_v(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }

@@ -216,8 +216,11 @@ __global__ void __launch_bounds__(NTH) k_far(int64_t N, int np, const typename V
     if (t >= N) continue;
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
-      double v = (sizeof(R) == 4) ? (double)tot[j][o].hi + (double)tot[j][o].lo : (double)acc[j][o];
-      part[((int64_t)blockIdx.y * NO + o) * N + t] = v;
+      const int64_t k = ((int64_t)blockIdx.y * NO + o) * N + t;
+      if (sizeof(R) == 4)  // float32 partials as (hi, lo) pairs
+        reinterpret_cast<float2*>(part)[k] = make_float2(tot[j][o].hi, tot[j][o].lo);
+      else
+        part[k] = (double)acc[j][o];
     }
   }
 }
@@ -230,21 +233,6 @@ __global__ void __launch_bounds__(NTH) k_far(int64_t N, int np, const typename V
 // the longer kernels K2, KALL, K4; the short K1 measured faster scalar).  Sources
 // are staged as structure-of-arrays so that consecutive pairs load directly
 // as packed operands.  Tiles with near pairs fall back to the scalar loop.
-typedef unsigned long long u64;
-__device__ __forceinline__ u64 pk2(float a, float b) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void upk2(u64 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
-__device__ __forceinline__ u64 add2(u64 a, u64 b) { u64 r; asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
-__device__ __forceinline__ u64 sub2(u64 a, u64 b) { u64 r; asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
-__device__ __forceinline__ u64 mul2(u64 a, u64 b) { u64 r; asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b)); return r; }
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-  u64 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
 __device__ __forceinline__ u64 rsqrt2(u64 x) {
   float a, b;
   upk2(x, a, b);
@@ -412,7 +400,8 @@ __global__ void __launch_bounds__(NTH) k_far32x2(int64_t N, int np, const float4
     if (t >= N) continue;
 #pragma unroll
     for (int o = 0; o < NO; ++o)
-      part[((int64_t)blockIdx.y * NO + o) * N + t] = (double)tot[j][o].hi + (double)tot[j][o].lo;
+      reinterpret_cast<float2*>(part)[((int64_t)blockIdx.y * NO + o) * N + t] =
+          make_float2(tot[j][o].hi, tot[j][o].lo);
   }
 }
 
@@ -636,17 +625,38 @@ __global__ void k_epilogue(int64_t N, int np, int nsplit, int nacc, const double
     }
     warp_reduce_scatter<4>(cs, lane);  // lane 8 o holds output o
   }
-  const int o = lane >> 3;
-  if ((lane & 7) != 0 || o >= sp.nout) return;
-  double f = 0;
-  if (sp.acc[o] >= 0) {
-    for (int s = 0; s < nsplit; ++s) f += part[((int64_t)s * nacc + sp.acc[o]) * N + i];
-  } else {
-    double g[3] = {0, 0, 0};
-    for (int s = 0; s < nsplit; ++s)
-      for (int k = 0; k < 3; ++k) g[k] += part[((int64_t)s * nacc + 1 + k) * N + i];
-    f = -(nrm[3 * i] * g[0] + nrm[3 * i + 1] * g[1] + nrm[3 * i + 2] * g[2]);
-  }
+  // split partials of output o summed by lanes 8 o .. 8 o + 7, eight splits
+  // apart (float64 for float64 passes, else (hi, lo) float pairs summed in
+  // double-float arithmetic), then combined by three shuffles
+  const int o = lane >> 3, sub = lane & 7;
+  const int oo = o < sp.nout ? o : 0;
+  const int a0 = sp.acc[oo];
+  using P = typename std::conditional<MODE == 0, double, F2>::type;
+  P g[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) g[k] = P{};
+  const int na = a0 >= 0 ? 1 : 3;
+  const int ab = a0 >= 0 ? a0 : 1;
+  for (int s = sub; s < nsplit; s += 8)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (k >= na) break;
+      const int64_t idx = ((int64_t)s * nacc + ab + k) * N + i;
+      if constexpr (MODE == 0) {
+        g[k] += part[idx];
+      } else {
+        const float2 v = reinterpret_cast<const float2*>(part)[idx];
+        g[k] = df_add(g[k], {v.x, v.y});
+      }
+    }
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = add_v(g[k], shfl_xor_v(g[k], off));
+  if (sub != 0 || o >= sp.nout) return;
+  double f;
+  if (a0 >= 0) f = to_d(g[0]);
+  else f = -(nrm[3 * i] * to_d(g[0]) + nrm[3 * i + 1] * to_d(g[1]) + nrm[3 * i + 2] * to_d(g[2]));
   sp.out[o][i] = f * sp.scale[o] + (corr ? to_d(cs[0]) : 0.0);
 }
 
@@ -700,21 +710,23 @@ static int lowp_dens(lb_ctx* c, int mode, EpiSpec& sp) {
 
 static int run_epilogue(lb_ctx* c, int prec, int nsplit, int nacc, const double* part, EpiSpec sp) {
   const unsigned grid = lb_div_up(c->N * 32, 256);
-  const int mode = (!c->have_corr || prec == LB_FP64) ? 0 : (prec == LB_FP32 ? 1 : 2);
-  if (mode) {
+  // the pair precision fixes the partials' format and the correction arithmetic
+  const int mode = prec == LB_FP64 ? 0 : (prec == LB_FP32 ? 1 : 2);
+  const bool corr = c->have_corr;
+  if (mode && corr) {
     LB_CHECK(lb_lowp_vals(c));
     LB_CHECK(lowp_dens(c, mode, sp));
   }
   ProfScope prof(c, LB_PROF_EPILOGUE);
   if (mode == 0)
     k_epilogue<0><<<grid, 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr, c->near_patch,
-                                               c->have_corr ? c->vals : nullptr, nullptr, nullptr, sp);
+                                               corr ? c->vals : nullptr, nullptr, nullptr, sp);
   else if (mode == 1)
     k_epilogue<1><<<grid, 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr, c->near_patch,
-                                               nullptr, c->vals_hi, nullptr, sp);
+                                               nullptr, corr ? c->vals_hi : nullptr, nullptr, sp);
   else
     k_epilogue<2><<<grid, 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr, c->near_patch,
-                                               nullptr, c->vals_hi, c->vals_lo, sp);
+                                               nullptr, corr ? c->vals_hi : nullptr, corr ? c->vals_lo : nullptr, sp);
   LB_LAUNCH(c);
   return LB_OK;
 }
@@ -929,8 +941,16 @@ extern "C" int lb_far_sums(lb_ctx* c, int precision, int nrhs, const double* sig
       sp.kern[k] = -1;
       sp.out[k] = dout + ((int64_t)r * 4 + k) * N;
     }
-    k_epilogue<0><<<lb_div_up(N * 32, 256), 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr,
-                                                                  c->near_patch, nullptr, nullptr, nullptr, sp);
+    const unsigned grid = lb_div_up(N * 32, 256);
+    if (precision == LB_FP64)
+      k_epilogue<0><<<grid, 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr, c->near_patch, nullptr,
+                                                 nullptr, nullptr, sp);
+    else if (precision == LB_FP32)
+      k_epilogue<1><<<grid, 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr, c->near_patch, nullptr,
+                                                 nullptr, nullptr, sp);
+    else
+      k_epilogue<2><<<grid, 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr, c->near_patch, nullptr,
+                                                 nullptr, nullptr, sp);
     LB_LAUNCH(c);
   }
   return lb_stage_out_finish(c, out, dout, nrhs * 4 * N * sizeof(double));
@@ -1105,7 +1125,7 @@ extern "C" int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, cons
     sp.kern[k] = -1;
     sp.out[k] = out + (int64_t)k * N;
   }
-  k_epilogue<0><<<lb_div_up(N * 32, 256), 256, 0, st>>>(N, np, (int)nsplit, 4, part, nrm, row_ptr, near_patch,
+  k_epilogue<1><<<lb_div_up(N * 32, 256), 256, 0, st>>>(N, np, (int)nsplit, 4, part, nrm, row_ptr, near_patch,
                                                         nullptr, nullptr, nullptr, sp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return lb_fail(nullptr, LB_ECUDA, "lb_far_sums_noalloc launch: %s", cudaGetErrorString(e));

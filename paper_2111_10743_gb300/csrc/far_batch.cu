@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(BT_NTH) k_farb32(int64_t N, int np, const floa
   for (int r = 0; r < RC; ++r)
 #pragma unroll
     for (int o = 0; o < NO; ++o)
-      part[(((int64_t)blockIdx.y * RC + r) * NO + o) * N + t] = (double)tot[r][o].hi + (double)tot[r][o].lo;
+      reinterpret_cast<float2*>(part)[(((int64_t)blockIdx.y * RC + r) * NO + o) * N + t] =
+          make_float2(tot[r][o].hi, tot[r][o].lo);
 }
 
 // double-float.  G: four planes of Npad float4 (x hi, x lo, n hi, n lo; the
@@ -267,7 +268,8 @@ __global__ void __maxnreg__(200) k_farbdf(int64_t N, int64_t Npad, int np, const
   for (int r = 0; r < RC; ++r)
 #pragma unroll
     for (int o = 0; o < NO; ++o)
-      part[(((int64_t)blockIdx.y * RC + r) * NO + o) * N + t] = (double)acc[r][o].h + (double)acc[r][o].l;
+      reinterpret_cast<float2*>(part)[(((int64_t)blockIdx.y * RC + r) * NO + o) * N + t] =
+          make_float2(acc[r][o].h, acc[r][o].l);
 }
 
 // ---------------------------------------------------------------------------
@@ -391,9 +393,14 @@ __global__ void k_epib(int64_t N, int np, int R, int nsplit, const double* __res
   if constexpr (MODE == 1) cmine = (double)cs[0];
   else cmine = df_to_double(cs[0]);
   const int rr = lane >> 2, o = lane & 3;
-  double a = 0.0;
+  // split partials: (hi, lo) float pairs summed in double-float arithmetic
+  F2 as = {0.f, 0.f};
   if (rr < RC && rr < R)
-    for (int s = 0; s < nsplit; ++s) a += part[(((int64_t)s * RC + rr) * 4 + o) * N + i];
+    for (int s = 0; s < nsplit; ++s) {
+      const float2 v = reinterpret_cast<const float2*>(part)[(((int64_t)s * RC + rr) * 4 + o) * N + i];
+      as = df_add(as, {v.x, v.y});
+    }
+  const double a = df_to_double(as);
   if (!PASS2) {
     const int base = lane & ~3;
     const double g1 = __shfl_sync(0xffffffffu, a, base + 1);

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(NTH) k_far_df(int64_t N, int np, const float4*
     if (t >= N) continue;
 #pragma unroll
     for (int o = 0; o < NO; ++o)
-      part[((int64_t)blockIdx.y * NO + o) * N + t] = (double)acc[j][o].h + (double)acc[j][o].l;
+      reinterpret_cast<float2*>(part)[((int64_t)blockIdx.y * NO + o) * N + t] = make_float2(acc[j][o].h, acc[j][o].l);
   }
 }
 
