@@ -79,6 +79,8 @@ typedef struct {
   double tol;           /* relative residual target |b - A x| / |b|; default 1e-10 */
   double inner_tol;     /* LB_FP32_REFINED: inner GMRES relative tolerance; default 1e-5 */
   int max_refine;       /* LB_FP32_REFINED: outer refinement steps cap; default 6 */
+  int graphs;           /* 1: lockstep solves replay each GMRES iteration as a captured CUDA graph
+                           (while per-kernel profiling is off); 0: plain launches; default 1 */
 } lb_params;
 
 typedef struct {
@@ -93,6 +95,7 @@ typedef struct {
   double history[128];      /* relative residual estimate per GMRES iteration, first rhs */
   int32_t history_len;
   int64_t pairs;            /* far-field pair interactions evaluated by the solve */
+  int32_t graph_iterations; /* lockstep GMRES iterations run as CUDA-graph replays */
 } lb_solve_info;
 
 typedef struct {

@@ -31,7 +31,8 @@ class lb_params(ctypes.Structure):
     _fields_ = [("eps_quad", ctypes.c_double), ("near_factor", ctypes.c_double),
                 ("precision", ctypes.c_int), ("formulation", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
-                ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int)]
+                ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("graphs", ctypes.c_int)]
 
 
 class lb_solve_info(ctypes.Structure):
@@ -40,14 +41,15 @@ class lb_solve_info(ctypes.Structure):
                 ("applies_fp32", ctypes.c_int32), ("nrhs", ctypes.c_int32),
                 ("rel_residual", ctypes.c_double), ("removed_mean", ctypes.c_double),
                 ("history", ctypes.c_double * 128), ("history_len", ctypes.c_int32),
-                ("pairs", ctypes.c_int64)]
+                ("pairs", ctypes.c_int64), ("graph_iterations", ctypes.c_int32)]
 
     def as_dict(self):
         return {"iterations": self.iterations, "refinements": self.refinements,
                 "converged": bool(self.converged), "applies_fp64": self.applies_fp64,
                 "applies_fp32": self.applies_fp32, "nrhs": self.nrhs,
                 "rel_residual": self.rel_residual, "removed_mean": self.removed_mean,
-                "history": list(self.history[:self.history_len]), "pairs": self.pairs}
+                "history": list(self.history[:self.history_len]), "pairs": self.pairs,
+                "graph_iterations": self.graph_iterations}
 
 
 class lb_geom_info(ctypes.Structure):

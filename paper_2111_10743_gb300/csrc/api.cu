@@ -19,6 +19,7 @@
 
 thread_local int64_t lb_pair_counter = 0;
 thread_local int lb_apply64_counter = 0, lb_apply32_counter = 0;
+thread_local int lb_graph_counter = 0;
 
 static char g_static_err[512] = "no error";
 
@@ -102,7 +103,10 @@ ProfScope::ProfScope(lb_ctx* ctx, int category, int64_t npairs) : c(ctx), cat(ca
   }
   a = c->ev_pool.back();
   c->ev_pool.pop_back();
-  cudaEventRecord(a, c->stream);
+  // inside a stream capture the record becomes a node of the graph, timed
+  // again at every replay
+  if (c->capture_prof) cudaEventRecordWithFlags(a, c->stream, cudaEventRecordExternal);
+  else cudaEventRecord(a, c->stream);
 }
 
 ProfScope::~ProfScope() {
@@ -114,8 +118,13 @@ ProfScope::~ProfScope() {
     b = c->ev_pool.back();
     c->ev_pool.pop_back();
   }
-  cudaEventRecord(b, c->stream);
-  c->prof_pending.push_back({cat, a, b, pairs});
+  if (c->capture_prof) {
+    cudaEventRecordWithFlags(b, c->stream, cudaEventRecordExternal);
+    c->capture_prof->push_back({cat, a, b, pairs});
+  } else {
+    cudaEventRecord(b, c->stream);
+    c->prof_pending.push_back({cat, a, b, pairs});
+  }
 }
 
 static int prof_resolve(lb_ctx* c) {
@@ -168,6 +177,7 @@ extern "C" int lb_default_params(lb_params* p) {
   p->tol = 1e-10;
   p->inner_tol = 1e-5;
   p->max_refine = 6;
+  p->graphs = 1;
   return LB_OK;
 }
 
@@ -181,6 +191,7 @@ static int check_params(lb_ctx* c, const lb_params* p) {
   if (!(p->tol > 0 && p->tol < 1)) return lb_fail(c, LB_EINVAL, "tol must be in (0,1)");
   if (!(p->inner_tol > 0 && p->inner_tol < 1)) return lb_fail(c, LB_EINVAL, "inner_tol must be in (0,1)");
   if (p->max_refine < 1 || p->max_refine > 100) return lb_fail(c, LB_EINVAL, "max_refine must be in [1,100]");
+  if (p->graphs != 0 && p->graphs != 1) return lb_fail(c, LB_EINVAL, "graphs must be 0 or 1");
   return LB_OK;
 }
 
@@ -244,6 +255,7 @@ extern "C" int lb_destroy(lb_ctx* c) {
                     &c->ws_stage_out, &c->ws_gm, &c->ws_quad, &c->ws_bpot, &c->ws_bgm, &c->ws_bvec, &c->ws_dlow})
     if (b->p) cudaFree(b->p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto& p : c->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;

@@ -466,8 +466,15 @@ __global__ void k_a3_final_batch(int64_t N, const double* __restrict__ tau, cons
 // the grid fills whole waves of resident blocks
 template <typename F>
 static int pick_nsplit(lb_ctx* c, F kernel, int64_t ntb, int64_t ntiles, int* out) {
+  // queried once per kernel: the launches of a captured iteration make no queries
   int per_sm = 0;
-  LB_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BT_NTH, 0));
+  auto it = c->occupancy.find((const void*)kernel);
+  if (it != c->occupancy.end()) {
+    per_sm = it->second;
+  } else {
+    LB_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BT_NTH, 0));
+    c->occupancy[(const void*)kernel] = per_sm;
+  }
   const int64_t slots = (int64_t)std::max(per_sm, 1) * c->sm_count;
   int best = 1;
   double best_eff = -1;

@@ -6,6 +6,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -46,6 +47,7 @@ struct ProfPending {
 struct lb_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream for graph captures (made on first use)
   lb_params params{};
   int sm_count = 0;
   std::string err;
@@ -91,9 +93,11 @@ struct lb_ctx {
   float* vals_hi = nullptr;     // [nnzb][4][np] float32 copy (double-float hi part), made on first use
   float* vals_lo = nullptr;     // [nnzb][4][np] double-float lo part
   std::vector<MaskTable> masks;
+  std::map<const void*, int> occupancy;  // resident blocks per SM, per kernel (queried once)
 
   // profiling
   int prof_on = 0;
+  std::vector<ProfPending>* capture_prof = nullptr;  // set while a graph is being captured
   int64_t launches = 0;
   std::vector<ProfPending> prof_pending;
   std::vector<cudaEvent_t> ev_pool;
@@ -194,5 +198,6 @@ int lb_wmean(lb_ctx* c, const double* f, double* mean_host);
 // counters of the last solve
 extern thread_local int64_t lb_pair_counter;
 extern thread_local int lb_apply64_counter, lb_apply32_counter;
+extern thread_local int lb_graph_counter;  // GMRES iterations run as graph replays
 
 static inline unsigned lb_div_up(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }

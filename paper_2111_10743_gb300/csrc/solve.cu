@@ -403,74 +403,260 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
 // The R systems advance together: each GMRES iteration applies A3 once to
 // the current basis vectors of all systems still iterating (one batched
 // far-field pass per A3 pass, several densities per pair evaluation), then
-// runs the Arnoldi step of each system.  The j-th basis vectors of all
-// systems are adjacent ([m+1][R][N]), so with every system active the batched
-// apply reads them in place; once some have converged, the active ones are
-// gathered first.  A system stops when its own residual estimate is below
-// tol, exactly as it would alone.
+// runs the Arnoldi step of those systems in kernels that cover all of them
+// at once (blockIdx.y = system).  A system stops when its own residual
+// estimate is below tol, exactly as it would alone.
+//
+// The iteration index j lives on the device and the active systems travel
+// as a kernel argument, so one iteration is a fixed sequence of launches:
+// captured once as a CUDA graph per active set and replayed (parameter
+// `graphs`, unless per-kernel profiling is on), or launched directly; both
+// run the same kernels on the same data and give identical results.
+//
+// Workspace: V [m+1][R][N] (the j-th vectors of all systems adjacent), the
+// gathered apply input and its output [R][N], split partials of the
+// multi-dots, and per system a small block: h, the Hessenberg columns, the
+// rotations, g, y and scalars (residual, squared norms, beta).
+struct LkAct {
+  int n;
+  int r[LB_BATCH_MAX];
+};
+
+struct LkDev {
+  int64_t N;
+  int R, m, ldh;
+  int64_t SM;          // doubles per system's small block
+  double* V;           // [m+1][R][N]
+  double* small;       // [R][SM]
+  double* partial;     // [R][m+2][GM_RB]
+  int* jdev;           // iteration index
+  double* resbuf;      // [R] residual estimates of the active systems, in act order
+};
+
+// offsets inside a system's small block
+#define LK_H(d) 0
+#define LK_HM(d) ((d).m + 2)
+#define LK_CS(d) (LK_HM(d) + (int64_t)(d).ldh * (d).m)
+#define LK_SN(d) (LK_CS(d) + (d).m + 2)
+#define LK_G(d) (LK_SN(d) + (d).m + 2)
+#define LK_Y(d) (LK_G(d) + (d).m + 2)
+#define LK_SC(d) (LK_Y(d) + (d).m + 2)  // [0] residual, [1] r, [2] |w|^2, [4] |b|^2, [5] beta
+#define LK_SMALL(m) ((int64_t)((m) + 2) * 5 + (int64_t)((m) + 1) * (m) + 8)
+
+// in[a] = V[j][act[a]]
+__global__ void k_lk_gather(LkDev d, LkAct act, double* __restrict__ in) {
+  const int a = blockIdx.y, r = act.r[a];
+  const double* src = d.V + ((int64_t)(*d.jdev) * d.R + r) * d.N;
+  double* dst = in + (int64_t)a * d.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// per-block partial dot products of w_a with V_r[0..j] (self = 0) or with
+// itself (self = 1): partial[a][v][blk]
+__global__ void k_lk_dots(LkDev d, LkAct act, const double* __restrict__ W, int self) {
+  __shared__ double sh[256];
+  const int a = blockIdx.y, r = act.r[a];
+  const double* w = W + (int64_t)a * d.N;
+  const int nvec = self ? 1 : *d.jdev + 1;
+  for (int v = 0; v < nvec; ++v) {
+    const double* x = self ? w : d.V + ((int64_t)v * d.R + r) * d.N;
+    double s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * blockDim.x)
+      s += x[i] * w[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+      if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) d.partial[((int64_t)a * (d.m + 2) + v) * gridDim.x + blockIdx.x] = sh[0];
+    __syncthreads();
+  }
+}
+
+// small_r[off + v] = ordered sum of the partials of vector v
+__global__ void k_lk_reduce(LkDev d, LkAct act, int self, int64_t off, int nblk) {
+  const int a = blockIdx.y, r = act.r[a];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvec = self ? 1 : *d.jdev + 1;
+  if (v >= nvec) return;
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += d.partial[((int64_t)a * (d.m + 2) + v) * nblk + b];
+  d.small[(int64_t)r * d.SM + off + v] = s;
+}
+
+// w_a -= sum_{v <= j} small_r[off + v] V_r[v]
+__global__ void k_lk_axpy(LkDev d, LkAct act, double* __restrict__ W, int64_t off) {
+  const int a = blockIdx.y, r = act.r[a];
+  const int nvec = *d.jdev + 1;
+  const double* c = d.small + (int64_t)r * d.SM + off;
+  double* w = W + (int64_t)a * d.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int v = 0; v < nvec; ++v) s -= c[v] * d.V[((int64_t)v * d.R + r) * d.N + i];
+    w[i] = s;
+  }
+}
+
+// h += y (the second Gram-Schmidt pass's coefficients)
+__global__ void k_lk_addsmall(LkDev d, LkAct act) {
+  const int a = blockIdx.y, r = act.r[a];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v > *d.jdev) return;
+  double* sm = d.small + (int64_t)r * d.SM;
+  sm[LK_H(d) + v] += sm[LK_Y(d) + v];
+}
+
+// h_{j+1} = |w|, V_r[j+1] = w / |w| (zero when |w| = 0)
+__global__ void k_lk_normalize(LkDev d, LkAct act, const double* __restrict__ W) {
+  const int a = blockIdx.y, r = act.r[a];
+  const int j = *d.jdev;
+  double* sm = d.small + (int64_t)r * d.SM;
+  const double hn = sqrt(sm[LK_SC(d) + 2]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sm[LK_H(d) + j + 1] = hn;
+  const double inv = hn != 0.0 ? 1.0 / hn : 0.0;
+  const double* w = W + (int64_t)a * d.N;
+  double* vn = d.V + ((int64_t)(j + 1) * d.R + r) * d.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * blockDim.x)
+    vn[i] = w[i] * inv;
+}
+
+// Givens update of column j for each active system; residual estimate
+// |g_{j+1}| / beta into its scalars and into resbuf[a]
+__global__ void k_lk_givens(LkDev d, LkAct act) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= act.n) return;
+  const int r = act.r[a];
+  const int j = *d.jdev;
+  double* sm = d.small + (int64_t)r * d.SM;
+  const double* h = sm + LK_H(d);
+  double* col = sm + LK_HM(d) + (int64_t)j * d.ldh;
+  double* cs = sm + LK_CS(d);
+  double* sn = sm + LK_SN(d);
+  double* g = sm + LK_G(d);
+  double* sc = sm + LK_SC(d);
+  for (int i = 0; i <= j + 1; ++i) col[i] = h[i];
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double x = col[j], y = col[j + 1];
+  const double rr = hypot(x, y);
+  const double cc = rr > 0 ? x / rr : 1.0, ss = rr > 0 ? y / rr : 0.0;
+  cs[j] = cc;
+  sn[j] = ss;
+  col[j] = rr;
+  col[j + 1] = 0.0;
+  g[j + 1] = -ss * g[j];
+  g[j] = cc * g[j];
+  sc[0] = fabs(g[j + 1]) / sc[5];
+  sc[1] = rr;
+  d.resbuf[a] = sc[0];
+}
+
+__global__ void k_lk_advance(LkDev d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ++*d.jdev;
+}
+
+// start: beta_r = |b_r|, g_r = (beta_r, 0, ...), V_r[0] = b_r / beta_r
+__global__ void k_lk_start(LkDev d, LkAct act, const double* __restrict__ b) {
+  const int a = blockIdx.y, r = act.r[a];
+  double* sm = d.small + (int64_t)r * d.SM;
+  const double beta = sqrt(sm[LK_SC(d) + 4]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sm[LK_SC(d) + 5] = beta;
+  const double inv = beta != 0.0 ? 1.0 / beta : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * blockDim.x)
+    d.V[(int64_t)r * d.N + i] = b[(int64_t)r * d.N + i] * inv;
+  if (blockIdx.x == 0)
+    for (int v = threadIdx.x; v < d.m + 2; v += blockDim.x) sm[LK_G(d) + v] = v == 0 ? beta : 0.0;
+}
+
+// back substitution and x_r = V_r y_r for system r with k_r iterations
+__global__ void k_lk_backsolve(LkDev d, int r, int k) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* sm = d.small + (int64_t)r * d.SM;
+  const double* Hm = sm + LK_HM(d);
+  const double* g = sm + LK_G(d);
+  double* y = sm + LK_Y(d);
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int l = i + 1; l < k; ++l) s -= Hm[(int64_t)l * d.ldh + i] * y[l];
+    const double dd = Hm[(int64_t)i * d.ldh + i];
+    y[i] = dd != 0.0 ? s / dd : 0.0;
+  }
+}
+
 struct Lockstep {
   int R = 0, m = 0;
-  double* V = nullptr;   // [m+1][R][N]
-  double* in = nullptr;  // [R][N] gathered apply input
-  double* out = nullptr; // [R][N] apply output
-  std::vector<Gm> G;
+  LkDev d{};
+  double* in = nullptr;   // [R][N] gathered apply input
+  double* out = nullptr;  // [R][N] apply output
 };
 
 static int lockstep_work(lb_ctx* c, int R, int m, Lockstep* L) {
   const int64_t N = c->N;
-  const int ldh = m + 1;
-  const size_t small = (size_t)(m + 2) * 5 + (size_t)ldh * m + 8;
-  const size_t need = (size_t)(m + 1) * R * N + 2 * (size_t)R * N + (size_t)GM_RB * (m + 2) + small * R;
+  const int64_t SM = LK_SMALL(m);
+  const size_t need = (size_t)(m + 1) * R * N + 2 * (size_t)R * N + (size_t)R * (m + 2) * GM_RB +
+                      (size_t)R * SM + (size_t)R + 8;
   LB_CHECK(lb_ensure(c, c->ws_bgm, need * sizeof(double)));
   double* p = (double*)c->ws_bgm.p;
   L->R = R;
   L->m = m;
-  L->V = p; p += (size_t)(m + 1) * R * N;
+  LkDev& d = L->d;
+  d.N = N;
+  d.R = R;
+  d.m = m;
+  d.ldh = m + 1;
+  d.SM = SM;
+  d.V = p; p += (size_t)(m + 1) * R * N;
   L->in = p; p += (size_t)R * N;
   L->out = p; p += (size_t)R * N;
-  double* partial = p; p += (size_t)GM_RB * (m + 2);
-  L->G.assign(R, Gm{});
-  for (int r = 0; r < R; ++r) {
-    Gm& G = L->G[r];
-    G.m = m;
-    G.ldh = ldh;
-    G.ldv = (int64_t)R * N;
-    G.V = L->V + (int64_t)r * N;
-    G.partial = partial;
-    G.h = p; p += m + 2;
-    G.Hm = p; p += (size_t)ldh * m;
-    G.cs = p; p += m + 2;
-    G.sn = p; p += m + 2;
-    G.g = p; p += m + 2;
-    G.y = p; p += m + 2;
-    G.scal = p; p += 8;
-    G.w = nullptr;
-  }
+  d.partial = p; p += (size_t)R * (m + 2) * GM_RB;
+  d.small = p; p += (size_t)R * SM;
+  d.resbuf = p; p += R;
+  d.jdev = (int*)p;
   return LB_OK;
 }
 
-// device scalars d[k] (one per listed system) -> host, one synchronisation
-static int read_scalars(lb_ctx* c, const std::vector<const double*>& d, std::vector<double>* h) {
-  if ((int)d.size() > LB_PINNED_DOUBLES) return lb_fail(c, LB_EINVAL, "too many systems in one readback");
-  for (size_t k = 0; k < d.size(); ++k)
-    LB_CUDA(c, cudaMemcpyAsync(c->host_pinned + k, d[k], sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+static LkAct make_act(const std::vector<int>& sys) {
+  LkAct a{};
+  a.n = (int)sys.size();
+  for (int k = 0; k < a.n; ++k) a.r[k] = sys[k];
+  return a;
+}
+
+// squared norms |v_r|^2 of the listed systems into their scalars [4];
+// returns the norms on the host
+static int lk_norms(lb_ctx* c, Lockstep& L, const double* v, const std::vector<int>& sys, std::vector<double>* out) {
+  if (sys.empty()) { out->clear(); return LB_OK; }
+  const LkAct act = make_act(sys);
+  LkDev d = L.d;
+  k_lk_dots<<<dim3(GM_RB, act.n), 256, 0, c->stream>>>(d, act, v, 1);
+  LB_LAUNCH(c);
+  k_lk_reduce<<<dim3(1, act.n), 64, 0, c->stream>>>(d, act, 1, LK_SC(d) + 4, GM_RB);
+  LB_LAUNCH(c);
+  for (int a = 0; a < act.n; ++a)
+    LB_CUDA(c, cudaMemcpyAsync(c->host_pinned + a, d.small + (int64_t)act.r[a] * d.SM + LK_SC(d) + 4, sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream));
   LB_CUDA(c, cudaStreamSynchronize(c->stream));
-  h->assign(c->host_pinned, c->host_pinned + d.size());
+  out->resize(act.n);
+  for (int a = 0; a < act.n; ++a) (*out)[a] = sqrt(c->host_pinned[a]);
   return LB_OK;
 }
 
-// |v_r| for the listed systems of v [R][N]
+// the norms_of helper of the refinement: v [R][N], listed systems
 static int norms_of(lb_ctx* c, Lockstep& L, const double* v, const std::vector<int>& sys, std::vector<double>* out) {
-  std::vector<const double*> d;
-  for (int r : sys) {
-    Gm& G = L.G[r];
-    const double* vr = v + (int64_t)r * c->N;
-    LB_CHECK(dots(c, G, 1, vr, vr, G.scal + 4, 0));
-    d.push_back(G.scal + 4);
-  }
-  LB_CHECK(read_scalars(c, d, out));
-  for (double& x : *out) x = sqrt(x);
-  return LB_OK;
+  // lk_norms reads row a of its input for system act[a]: gather the rows
+  // into L.in first when they are not already in system order
+  bool ident = true;
+  for (size_t a = 0; a < sys.size(); ++a) ident = ident && sys[a] == (int)a;
+  if (ident) return lk_norms(c, L, v, sys, out);
+  for (size_t a = 0; a < sys.size(); ++a)
+    LB_CUDA(c, cudaMemcpyAsync(L.in + (int64_t)a * c->N, v + (int64_t)sys[a] * c->N, c->N * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->stream));
+  return lk_norms(c, L, L.in, sys, out);
 }
 
 // dst[a] = src[sys[a]] (rows of N doubles)
@@ -481,71 +667,194 @@ static int gather_rows(lb_ctx* c, const double* src, const std::vector<int>& sys
   return LB_OK;
 }
 
+// one lockstep iteration for the active set, enqueued on the context stream
+// (direct launches or stream capture); ends with the residual estimates of
+// the active systems copied to host_pinned[0..n)
+static int lk_iteration(lb_ctx* c, Lockstep& L, int prec, const LkAct& act) {
+  const LkDev d = L.d;
+  const unsigned nb = vec_blocks(c);
+  const dim3 gv(nb, act.n), gd(GM_RB, act.n), gs(lb_div_up(d.m + 2, 64), act.n);
+  k_lk_gather<<<gv, 256, 0, c->stream>>>(d, act, L.in);
+  LB_LAUNCH(c);
+  LB_CHECK(lb_apply_a3_batch(c, prec, act.n, L.in, L.out, nullptr));
+  // classical Gram-Schmidt, twice: h = V^T w, w -= V h, y = V^T w, w -= V y, h += y
+  k_lk_dots<<<gd, 256, 0, c->stream>>>(d, act, L.out, 0);
+  LB_LAUNCH(c);
+  k_lk_reduce<<<gs, 64, 0, c->stream>>>(d, act, 0, LK_H(d), GM_RB);
+  LB_LAUNCH(c);
+  k_lk_axpy<<<gv, 256, 0, c->stream>>>(d, act, L.out, LK_H(d));
+  LB_LAUNCH(c);
+  k_lk_dots<<<gd, 256, 0, c->stream>>>(d, act, L.out, 0);
+  LB_LAUNCH(c);
+  k_lk_reduce<<<gs, 64, 0, c->stream>>>(d, act, 0, LK_Y(d), GM_RB);
+  LB_LAUNCH(c);
+  k_lk_axpy<<<gv, 256, 0, c->stream>>>(d, act, L.out, LK_Y(d));
+  LB_LAUNCH(c);
+  k_lk_addsmall<<<gs, 64, 0, c->stream>>>(d, act);
+  LB_LAUNCH(c);
+  k_lk_dots<<<gd, 256, 0, c->stream>>>(d, act, L.out, 1);
+  LB_LAUNCH(c);
+  k_lk_reduce<<<dim3(1, act.n), 64, 0, c->stream>>>(d, act, 1, LK_SC(d) + 2, GM_RB);
+  LB_LAUNCH(c);
+  k_lk_normalize<<<gv, 256, 0, c->stream>>>(d, act, L.out);
+  LB_LAUNCH(c);
+  k_lk_givens<<<lb_div_up(act.n, 64), 64, 0, c->stream>>>(d, act);
+  LB_LAUNCH(c);
+  k_lk_advance<<<1, 32, 0, c->stream>>>(d);
+  LB_LAUNCH(c);
+  LB_CUDA(c, cudaMemcpyAsync(c->host_pinned, d.resbuf, act.n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return LB_OK;
+}
+
+// A captured iteration, the counters it advances per replay, and the
+// profiling events recorded inside it (timed again at every replay).
+struct LkGraph {
+  lb_ctx* c = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0, pairs = 0;
+  int a32 = 0, a64 = 0;
+  std::vector<ProfPending> prof;
+  void clear() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (auto& p : prof) { c->ev_pool.push_back(p.a); c->ev_pool.push_back(p.b); }
+    prof.clear();
+  }
+  ~LkGraph() { if (c) clear(); }
+};
+
+static int lk_capture(lb_ctx* c, Lockstep& L, int prec, const LkAct& act, LkGraph* g) {
+  g->c = c;
+  g->clear();
+  const int64_t l0 = c->launches, p0 = lb_pair_counter;
+  const int a32 = lb_apply32_counter, a64 = lb_apply64_counter;
+  // capture on the context's private stream (the caller's stream may be the
+  // legacy default stream, which cannot capture); the graph is replayed on
+  // the caller's stream, in order with its other work
+  if (!c->cap_stream) LB_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = c->stream;
+  LB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  c->stream = c->cap_stream;
+  c->capture_prof = &g->prof;
+  const int rc = lk_iteration(c, L, prec, act);
+  c->capture_prof = nullptr;
+  c->stream = user;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+  // the capture enqueued nothing: its counter increments belong to each replay
+  g->launches = c->launches - l0;
+  g->pairs = lb_pair_counter - p0;
+  g->a32 = lb_apply32_counter - a32;
+  g->a64 = lb_apply64_counter - a64;
+  c->launches = l0;
+  lb_pair_counter = p0;
+  lb_apply32_counter = a32;
+  lb_apply64_counter = a64;
+  if (rc != LB_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc != LB_OK ? rc : lb_fail(c, LB_ECUDA, "stream capture of the GMRES iteration failed: %s",
+                                      cudaGetErrorString(e));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    g->exec = nullptr;
+    return lb_fail(c, LB_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+  }
+  return LB_OK;
+}
+
+static int lk_replay(lb_ctx* c, LkGraph& g) {
+  LB_CUDA(c, cudaGraphLaunch(g.exec, c->stream));
+  c->launches += g.launches;
+  lb_pair_counter += g.pairs;
+  lb_apply32_counter += g.a32;
+  lb_apply64_counter += g.a64;
+  ++lb_graph_counter;
+  return LB_OK;
+}
+
+// after a replay has completed: add the times of its profiled launches
+static void lk_replay_profile(lb_ctx* c, const LkGraph& g) {
+  for (const auto& p : g.prof) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess && p.cat >= 0 && p.cat < LB_PROF_NCAT) {
+      c->prof_ms[p.cat] += ms;
+      c->prof_calls[p.cat] += 1;
+      c->prof_pairs[p.cat] += p.pairs;
+    }
+  }
+}
+
 // GMRES on R systems at once: b, x [R][N]; systems with b = 0 get x = 0
 static int gmres_lockstep(lb_ctx* c, Lockstep& L, int prec, const double* b, double* x, double tol, int max_iter,
                           std::vector<int>* its, std::vector<double>* res, std::vector<double>* hist0) {
   const int64_t N = c->N;
   const int R = L.R;
+  const LkDev d = L.d;
   const unsigned nb = vec_blocks(c);
   its->assign(R, 0);
   res->assign(R, 0.0);
   std::vector<int> all(R);
   for (int r = 0; r < R; ++r) all[r] = r;
   std::vector<double> beta;
-  LB_CHECK(norms_of(c, L, b, all, &beta));
+  LB_CHECK(lk_norms(c, L, b, all, &beta));
   std::vector<int> act;
   for (int r = 0; r < R; ++r) {
     if (!std::isfinite(beta[r])) return lb_fail(c, LB_EINVAL, "non-finite right-hand side");
-    Gm& G = L.G[r];
-    if (!(beta[r] > 0)) {
-      LB_CUDA(c, cudaMemsetAsync(x + (int64_t)r * N, 0, N * sizeof(double), c->stream));
-      continue;
-    }
-    act.push_back(r);
-    LB_CUDA(c, cudaMemsetAsync(G.g, 0, (G.m + 2) * sizeof(double), c->stream));
-    k_sqrt_to<<<1, 32, 0, c->stream>>>(G.scal + 4, G.g);
-    LB_LAUNCH(c);
-    k_scale_by<<<nb, 256, 0, c->stream>>>(N, b + (int64_t)r * N, G.g, G.V);
+    if (beta[r] > 0) act.push_back(r);
+    else LB_CUDA(c, cudaMemsetAsync(x + (int64_t)r * N, 0, N * sizeof(double), c->stream));
+  }
+  if (!act.empty()) {
+    const LkAct a0 = make_act(act);
+    k_lk_start<<<dim3(nb, a0.n), 256, 0, c->stream>>>(d, a0, b);
     LB_LAUNCH(c);
   }
+  LB_CUDA(c, cudaMemsetAsync(d.jdev, 0, sizeof(int), c->stream));
   if (hist0 && R > 0 && beta[0] > 0) hist0->push_back(1.0);
+  // graphs replay from the second iteration on: the first, launched
+  // directly, sizes every workspace the apply needs
+  bool use_graphs = c->params.graphs != 0;
+  LkGraph graph;
+  std::vector<int> captured;
   for (int j = 0; j < max_iter && !act.empty(); ++j) {
-    const int Ra = (int)act.size();
-    const double* Vj = L.V + (int64_t)j * R * N;
-    const double* in = Vj;
-    if (Ra < R) {
-      for (int a = 0; a < Ra; ++a)
-        LB_CUDA(c, cudaMemcpyAsync(L.in + (int64_t)a * N, Vj + (int64_t)act[a] * N, N * sizeof(double),
-                                   cudaMemcpyDeviceToDevice, c->stream));
-      in = L.in;
+    const LkAct a = make_act(act);
+    bool done = false;
+    if (use_graphs && j > 0) {
+      if (captured != act) {
+        if (lk_capture(c, L, prec, a, &graph) == LB_OK) {
+          captured = act;
+        } else {  // capture refused: plain launches from here on
+          cudaGetLastError();
+          use_graphs = false;
+        }
+      }
+      if (use_graphs) {
+        LB_CHECK(lk_replay(c, graph));
+        done = true;
+      }
     }
-    LB_CHECK(lb_apply_a3_batch(c, prec, Ra, in, L.out, nullptr));
-    std::vector<const double*> d;
-    for (int a = 0; a < Ra; ++a) {
-      Gm& G = L.G[act[a]];
-      G.w = L.out + (int64_t)a * N;
-      LB_CHECK(arnoldi_step(c, G, j, beta[act[a]]));
-      d.push_back(G.scal);
-    }
-    std::vector<double> rr;
-    LB_CHECK(read_scalars(c, d, &rr));
+    if (!done) LB_CHECK(lk_iteration(c, L, prec, a));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (done) lk_replay_profile(c, graph);
     std::vector<int> next;
-    for (int a = 0; a < Ra; ++a) {
-      const int r = act[a];
-      if (!std::isfinite(rr[a])) return lb_fail(c, LB_EINVAL, "GMRES breakdown: non-finite residual");
+    for (int k = 0; k < a.n; ++k) {
+      const int r = act[k];
+      const double rr = c->host_pinned[k];
+      if (!std::isfinite(rr)) return lb_fail(c, LB_EINVAL, "GMRES breakdown: non-finite residual");
       (*its)[r] = j + 1;
-      (*res)[r] = rr[a];
-      if (hist0 && r == 0) hist0->push_back(rr[a]);
-      if (!(rr[a] < tol || rr[a] == 0.0)) next.push_back(r);
+      (*res)[r] = rr;
+      if (hist0 && r == 0) hist0->push_back(rr);
+      if (!(rr < tol || rr == 0.0)) next.push_back(r);
     }
     act.swap(next);
   }
   for (int r = 0; r < R; ++r) {
     if (!(beta[r] > 0)) continue;
-    Gm& G = L.G[r];
-    k_backsolve<<<1, 32, 0, c->stream>>>((*its)[r], G.ldh, G.Hm, G.g, G.y);
+    k_lk_backsolve<<<1, 32, 0, c->stream>>>(d, r, (*its)[r]);
     LB_LAUNCH(c);
-    k_combine<<<nb, 256, 0, c->stream>>>(N, (*its)[r], G.V, G.ldv, G.y, x + (int64_t)r * N, 0);
+    k_combine<<<nb, 256, 0, c->stream>>>(N, (*its)[r], d.V + (int64_t)r * N, (int64_t)R * N,
+                                         d.small + (int64_t)r * d.SM + LK_Y(d), x + (int64_t)r * N, 0);
     LB_LAUNCH(c);
   }
   return LB_OK;
@@ -753,6 +1062,7 @@ extern "C" int lb_solve_lb(lb_ctx* c, int nrhs, const double* f, double* u, lb_s
   }
   lb_pair_counter = 0;
   lb_apply64_counter = lb_apply32_counter = 0;
+  lb_graph_counter = 0;
   const double* din;
   double* dout;
   LB_CHECK(lb_stage_in(c, f, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
@@ -763,6 +1073,7 @@ extern "C" int lb_solve_lb(lb_ctx* c, int nrhs, const double* f, double* u, lb_s
     info->pairs = lb_pair_counter;
     info->applies_fp64 = lb_apply64_counter;
     info->applies_fp32 = lb_apply32_counter;
+    info->graph_iterations = lb_graph_counter;
     LB_CUDA(c, cudaStreamSynchronize(c->stream));
     if (!info->converged) return lb_fail(c, LB_ENOTCONVERGED, "GMRES did not reach tol %.3g (residual %.3g)",
                                          c->params.tol, info->rel_residual);

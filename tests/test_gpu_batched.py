@@ -93,3 +93,32 @@ def test_lockstep_groups(lb):
     for r in (0, 63, 64, 65):
         u_ref, _, _, _ = solve_lb(d, f[r], "A3", tol=1e-12)
         assert _rel2(u[r], u_ref) < 1e-10, r
+
+
+@pytest.mark.parametrize("prec", ["df64", "fp32_refined"])
+def test_lockstep_graphs_match_direct_launches(lb, prec):
+    """Replaying each GMRES iteration as a captured CUDA graph runs the same
+    kernels on the same data as launching them directly: identical results,
+    and with profiling on every replayed far-field launch is still timed."""
+    from workloads.rhs import legendre_field
+    name = "torus1920"
+    s, d = oracle_disc(name)
+    rng = np.random.default_rng(35)
+    f = np.stack([legendre_field(d.geo.X, rng, 4, 2.75) for _ in range(5)])
+    kw = dict(formulation=lb.LB_A3, tol=1e-11,
+              precision=lb.LB_DF64 if prec == "df64" else lb.LB_FP32_REFINED)
+    out = {}
+    for graphs in (0, 1):
+        ctx, _, _ = ctx_for(lb, name, graphs=graphs, **kw)
+        out[graphs] = ctx.solve_lb(f)
+    (u0, i0), (u1, i1) = out[0], out[1]
+    assert i0["graph_iterations"] == 0 and i1["graph_iterations"] > 0
+    assert i0["iterations"] == i1["iterations"] and i0["pairs"] == i1["pairs"]
+    assert np.array_equal(u0, u1)
+    ctx.set_profiling(True)
+    u2, i2 = ctx.solve_lb(f)
+    prof = ctx.get_profile()
+    ctx.set_profiling(False)
+    assert i2["graph_iterations"] > 0 and np.array_equal(u2, u1)
+    far = sum(v["pairs"] for k, v in prof.items() if isinstance(v, dict) and k.startswith("far"))
+    assert far == i2["pairs"]
