@@ -304,6 +304,7 @@ def run_ours(args):
                 "ms_each": [round(x, 3) for x in e2e_ms],
                 "h2d_bytes_per_step": int(fh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8)},
         "gpu_launches": int(prof["launches"]),
+        "autotune": {k: v for k, v in ctx.get_tuning().items() if v},
         "clocks": clocks,
     }
     if ws == 1 and not args.no_cpu_baseline and not args.case.startswith("torus"):

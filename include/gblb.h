@@ -264,6 +264,14 @@ int lb_set_profiling(lb_ctx* ctx, int on);
  * lb_set_profiling. */
 int lb_get_profile(lb_ctx* ctx, lb_profile* out);
 
+/* Launch shapes chosen by the batched passes' tuner (not part of the paper;
+ * several-density passes time each shape once per process and surface and
+ * keep the fastest): shapes[8], indexed by precision (0 float32, 1
+ * double-float) * 4 + pass (0: A3 pass 1, 1: pass 2) * 2 + (0: 4 densities,
+ * 1: 8 densities per pass).  Values: 0 = 128 threads x 64-source tiles,
+ * 1 = 128 x 128, 2 = 256 x 64, -1 = not tuned yet.  Host memory. */
+int lb_get_tuning(lb_ctx* ctx, int* shapes);
+
 /* Far-field sums of one density that allocate nothing: the float32 pair
  * kernel of lb_far_sums with all of its scratch in a fixed device array that
  * the library carries (12 MiB, held on every GPU that loads the library until

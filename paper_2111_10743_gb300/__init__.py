@@ -94,7 +94,7 @@ def _load():
         "lb_apply_gradS": [P, ctypes.c_int, P, P], "lb_apply_A": [P, ctypes.c_int, P, P],
         "lb_solve_lb": [P, ctypes.c_int, P, P, P], "lb_harmonic_fields": [P, ctypes.c_int, P, P, P],
         "lb_surface_div": [P, ctypes.c_int, P, P],
-        "lb_set_profiling": [P, ctypes.c_int], "lb_get_profile": [P, P],
+        "lb_set_profiling": [P, ctypes.c_int], "lb_get_profile": [P, P], "lb_get_tuning": [P, P],
         "lb_far_sums_noalloc": [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
@@ -192,6 +192,18 @@ class Context:
 
     def set_profiling(self, on: bool = True):
         self._check(_lib.lb_set_profiling(self._h, 1 if on else 0))
+
+    def get_tuning(self) -> dict:
+        """Launch shapes picked by the batched passes' tuner (-1: not tuned)."""
+        a = (ctypes.c_int * 8)()
+        self._check(_lib.lb_get_tuning(self._h, a))
+        names = {0: "128x64", 1: "128x128", 2: "256x64", -1: None}
+        out = {}
+        for p, pn in enumerate(("far32", "fardf")):
+            for k, kn in enumerate(("k1", "k2")):
+                for r, rn in enumerate(("rc4", "rc8")):
+                    out[f"{pn}_{kn}_{rn}"] = names[a[p * 4 + k * 2 + r]]
+        return out
 
     def get_profile(self) -> dict:
         p = lb_profile()

@@ -13,13 +13,15 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "dfloat.cuh"
 #include "internal.cuh"
 
-#define BT_NTH 128
-#define BT_TS 64
 
 namespace {
 
@@ -52,8 +54,8 @@ __device__ __forceinline__ unsigned long long near_bits(bool any, int64_t t, int
 // float32.  P = (x - c, .), Nn = (n, .); charges Q[Npad][NPL*RC] (plane 0:
 // tau or mu1, plane 1: mu2), weighted by the quadrature weights.
 // part[split][r][o][N].
-template <int KIND, int RC>
-__global__ void __launch_bounds__(BT_NTH) k_farb32(int64_t N, int np, const float4* __restrict__ P,
+template <int KIND, int RC, int NTH, int TS>
+__global__ void __launch_bounds__(NTH) k_farb32(int64_t N, int np, const float4* __restrict__ P,
                                                    const float4* __restrict__ Nn, const float4* __restrict__ Q,
                                                    const uint8_t* __restrict__ flags, int64_t ntiles,
                                                    const int64_t* __restrict__ row_ptr,
@@ -63,11 +65,11 @@ __global__ void __launch_bounds__(BT_NTH) k_farb32(int64_t N, int np, const floa
   constexpr bool K2 = KIND == FAR_K2;
   constexpr int NQ4 = (K2 ? 2 : 1) * RC / 4;  // float4 charge groups per source
   static_assert(NQ4 >= 1, "RC must allow a float4 of charges");
-  __shared__ float4 sP[BT_TS];
-  __shared__ float4 sN[K2 ? BT_TS : 1];
-  __shared__ float4 sQ[BT_TS * NQ4];
-  __shared__ int sLp[BT_TS];
-  const int64_t t = (int64_t)blockIdx.x * BT_NTH + threadIdx.x;
+  __shared__ float4 sP[TS];
+  __shared__ float4 sN[K2 ? TS : 1];
+  __shared__ float4 sQ[TS * NQ4];
+  __shared__ int sLp[TS];
+  const int64_t t = (int64_t)blockIdx.x * NTH + threadIdx.x;
   const float4 tp = P[t];
   float nx = 0.f, ny = 0.f, nz = 0.f;
   if (K2) {
@@ -86,19 +88,19 @@ __global__ void __launch_bounds__(BT_NTH) k_farb32(int64_t N, int np, const floa
   const int64_t tile_b = (int64_t)blockIdx.y * tiles_per_split;
   const int64_t tile_e = min(ntiles, tile_b + tiles_per_split);
   for (int64_t tile = tile_b; tile < tile_e; ++tile) {
-    const int64_t s0 = tile * BT_TS;
+    const int64_t s0 = tile * TS;
     const int64_t P0 = s0 / np;
-    for (int s = threadIdx.x; s < BT_TS; s += BT_NTH) {
+    for (int s = threadIdx.x; s < TS; s += NTH) {
       sP[s] = P[s0 + s];
       if (K2) sN[s] = Nn[s0 + s];
       sLp[s] = (int)((s0 + s) / np - P0);
     }
-    for (int k = threadIdx.x; k < BT_TS * NQ4; k += BT_NTH) sQ[k] = Q[s0 * NQ4 + k];
+    for (int k = threadIdx.x; k < TS * NQ4; k += NTH) sQ[k] = Q[s0 * NQ4 + k];
     __syncthreads();
     const unsigned long long m =
         near_bits(flags[(int64_t)blockIdx.x * ntiles + tile] != 0, t, N, P0, row_ptr, near_patch);
 #pragma unroll 2
-    for (int s = 0; s < BT_TS; ++s) {
+    for (int s = 0; s < TS; ++s) {
       float q[NQ4 * 4];
 #pragma unroll
       for (int g = 0; g < NQ4; ++g) {
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(BT_NTH) k_farb32(int64_t N, int np, const floa
 // double-float.  G: four planes of Npad float4 (x hi, x lo, n hi, n lo; the
 // hi position on the exact-difference grid); charges Q[Npad][NPL*RC] of
 // float2 (hi, lo).
-template <int KIND, int RC>
+template <int KIND, int RC, int NTH, int TS>
 __global__ void __maxnreg__(200) k_farbdf(int64_t N, int64_t Npad, int np, const float4* __restrict__ G,
                                                    const float4* __restrict__ Q, const uint8_t* __restrict__ flags,
                                                    int64_t ntiles, const int64_t* __restrict__ row_ptr,
@@ -168,15 +170,15 @@ __global__ void __maxnreg__(200) k_farbdf(int64_t N, int64_t Npad, int np, const
   constexpr int NO = 4;
   constexpr bool K2 = KIND == FAR_K2;
   constexpr int NQ4 = (K2 ? 2 : 1) * RC / 2;  // float4 = two (hi, lo) charges
-  __shared__ float4 sA[BT_TS], sB[BT_TS];
-  __shared__ float4 sC[K2 ? BT_TS : 1], sD[K2 ? BT_TS : 1];
-  __shared__ float4 sQ[BT_TS * NQ4];
-  __shared__ int sLp[BT_TS];
+  __shared__ float4 sA[TS], sB[TS];
+  __shared__ float4 sC[K2 ? TS : 1], sD[K2 ? TS : 1];
+  __shared__ float4 sQ[TS * NQ4];
+  __shared__ int sLp[TS];
   const float4* GA = G;
   const float4* GB = G + Npad;
   const float4* GC = G + 2 * Npad;
   const float4* GD = G + 3 * Npad;
-  const int64_t t = (int64_t)blockIdx.x * BT_NTH + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * NTH + threadIdx.x;
   const float4 ta = GA[t], tb = GB[t];
   F2 nxx = {0.f, 0.f}, nxy = {0.f, 0.f}, nxz = {0.f, 0.f};
   if (K2) {
@@ -191,9 +193,9 @@ __global__ void __maxnreg__(200) k_farbdf(int64_t N, int64_t Npad, int np, const
   const int64_t tile_b = (int64_t)blockIdx.y * tiles_per_split;
   const int64_t tile_e = min(ntiles, tile_b + tiles_per_split);
   for (int64_t tile = tile_b; tile < tile_e; ++tile) {
-    const int64_t s0 = tile * BT_TS;
+    const int64_t s0 = tile * TS;
     const int64_t P0 = s0 / np;
-    for (int s = threadIdx.x; s < BT_TS; s += BT_NTH) {
+    for (int s = threadIdx.x; s < TS; s += NTH) {
       sA[s] = GA[s0 + s];
       sB[s] = GB[s0 + s];
       if (K2) {
@@ -202,11 +204,11 @@ __global__ void __maxnreg__(200) k_farbdf(int64_t N, int64_t Npad, int np, const
       }
       sLp[s] = (int)((s0 + s) / np - P0);
     }
-    for (int k = threadIdx.x; k < BT_TS * NQ4; k += BT_NTH) sQ[k] = Q[s0 * NQ4 + k];
+    for (int k = threadIdx.x; k < TS * NQ4; k += NTH) sQ[k] = Q[s0 * NQ4 + k];
     __syncthreads();
     const unsigned long long m =
         near_bits(flags[(int64_t)blockIdx.x * ntiles + tile] != 0, t, N, P0, row_ptr, near_patch);
-    for (int s = 0; s < BT_TS; ++s) {
+    for (int s = 0; s < TS; ++s) {
       const float4 A = sA[s], B = sB[s];
       const F2 dx = {ta.x - A.x, tb.x - B.x};
       const F2 dy = {ta.y - A.y, tb.y - B.y};
@@ -462,17 +464,31 @@ __global__ void k_a3_final_batch(int64_t N, const double* __restrict__ tau, cons
 }
 
 // ---------------------------------------------------------------------------
-// launch shape: the number of source splits (gridDim.y) is chosen so that
-// the grid fills whole waves of resident blocks
+// Launch shapes and their tuning.
+//
+// A batched pass can run with 128 or 256 threads per block (one target each)
+// and 64 or 128 sources per shared-memory tile; the number of source splits
+// (gridDim.y) is then chosen so that the grid fills whole waves of resident
+// blocks.  Which shape is fastest depends on the kernel, the density count
+// and N, so the first pass of each kind (not under a stream capture) times
+// every shape once on the real data with CUDA events and keeps the fastest
+// in a process-wide table: every later pass, every context of the process
+// and every graph replay then run that shape.  GBLB_BATCH_SHAPE = 0, 1 or 2
+// in the environment forces one shape.
+struct BShape {
+  int nth, ts;
+};
+static const BShape kShapes[3] = {{128, 64}, {128, 128}, {256, 64}};
+
 template <typename F>
-static int pick_nsplit(lb_ctx* c, F kernel, int64_t ntb, int64_t ntiles, int* out) {
+static int pick_nsplit(lb_ctx* c, F kernel, int nth, int64_t ntb, int64_t ntiles, int* out) {
   // queried once per kernel: the launches of a captured iteration make no queries
   int per_sm = 0;
   auto it = c->occupancy.find((const void*)kernel);
   if (it != c->occupancy.end()) {
     per_sm = it->second;
   } else {
-    LB_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, BT_NTH, 0));
+    LB_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nth, 0));
     c->occupancy[(const void*)kernel] = per_sm;
   }
   const int64_t slots = (int64_t)std::max(per_sm, 1) * c->sm_count;
@@ -496,54 +512,152 @@ static int pick_nsplit(lb_ctx* c, F kernel, int64_t ntb, int64_t ntiles, int* ou
 }
 
 // largest split count a batched launch can pick (workspace sizing)
-static int64_t max_nsplit(lb_ctx* c) { return std::min<int64_t>(c->Npad / BT_TS, 32); }
+static int64_t max_nsplit(lb_ctx* c) { return std::min<int64_t>(c->Npad / 64, 32); }
+
+// one far-field pass of shape (NTH, TS); Q (and G for double-float) packed
+template <int KIND, int RC, int NTH, int TS>
+static int far_shape(lb_ctx* c, bool df, const void* G, const void* Q, double* part, int* nsplit_out, int cat,
+                     int64_t pairs) {
+  MaskTable* m = nullptr;
+  LB_CHECK(lb_get_mask(c, NTH, TS, &m));
+  const int64_t ntb = m->ntb, ntiles = m->ntiles;
+  int nsplit = 1;
+  if (!df) {
+    auto kern = k_farb32<KIND, RC, NTH, TS>;
+    LB_CHECK(pick_nsplit(c, kern, NTH, ntb, ntiles, &nsplit));
+    const int tps = (int)((ntiles + nsplit - 1) / nsplit);
+    ProfScope prof(c, cat, pairs);
+    kern<<<dim3((unsigned)ntb, (unsigned)nsplit), NTH, 0, c->stream>>>(
+        c->N, c->np, c->pos32, c->nrm32, (const float4*)Q, m->flags, ntiles, c->row_ptr, c->near_patch, tps, part);
+    LB_LAUNCH(c);
+  } else {
+    auto kern = k_farbdf<KIND, RC, NTH, TS>;
+    LB_CHECK(pick_nsplit(c, kern, NTH, ntb, ntiles, &nsplit));
+    const int tps = (int)((ntiles + nsplit - 1) / nsplit);
+    ProfScope prof(c, cat, pairs);
+    kern<<<dim3((unsigned)ntb, (unsigned)nsplit), NTH, 0, c->stream>>>(
+        c->N, c->Npad, c->np, (const float4*)G, (const float4*)Q, m->flags, ntiles, c->row_ptr, c->near_patch, tps,
+        part);
+    LB_LAUNCH(c);
+  }
+  *nsplit_out = nsplit;
+  return LB_OK;
+}
+
+template <int KIND, int RC>
+static int far_any_shape(lb_ctx* c, int shape, bool df, const void* G, const void* Q, double* part, int* nsplit,
+                         int cat, int64_t pairs) {
+  switch (shape) {
+    case 1: return far_shape<KIND, RC, 128, 128>(c, df, G, Q, part, nsplit, cat, pairs);
+    case 2: return far_shape<KIND, RC, 256, 64>(c, df, G, Q, part, nsplit, cat, pairs);
+    default: return far_shape<KIND, RC, 128, 64>(c, df, G, Q, part, nsplit, cat, pairs);
+  }
+}
+
+namespace {
+struct TuneKey {
+  int device;
+  int64_t N;
+  int np, RC, kind, prec;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(device, N, np, RC, kind, prec) < std::tie(o.device, o.N, o.np, o.RC, o.kind, o.prec);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+}  // namespace
+
+// the shape for this pass: forced, tuned earlier, tuned now, or (under a
+// stream capture, where nothing may be timed) the first shape
+template <int KIND, int RC>
+static int tuned_shape(lb_ctx* c, bool df, const void* G, const void* Q, double* part, int* shape) {
+  if (const char* env = getenv("GBLB_BATCH_SHAPE")) {
+    const int s = atoi(env);
+    if (s >= 0 && s < 3) { *shape = s; return LB_OK; }
+  }
+  const TuneKey key{c->device, c->N, c->np, RC, KIND, df ? LB_DF64 : LB_FP32};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) { *shape = it->second; return LB_OK; }
+  }
+  *shape = 0;
+  if (c->capturing) return LB_OK;
+  cudaEvent_t e0, e1;
+  LB_CUDA(c, cudaEventCreate(&e0));
+  LB_CUDA(c, cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int best = 0, rc = LB_OK;
+  const int prof = c->prof_on;
+  c->prof_on = 0;  // tuning launches are not part of any profile
+  for (int s = 0; s < 3 && rc == LB_OK; ++s) {
+    int ns = 0;
+    rc = far_any_shape<KIND, RC>(c, s, df, G, Q, part, &ns, 0, 0);  // warm-up: mask table, caches
+    if (rc != LB_OK) break;
+    cudaEventRecord(e0, c->stream);
+    rc = far_any_shape<KIND, RC>(c, s, df, G, Q, part, &ns, 0, 0);
+    cudaEventRecord(e1, c->stream);
+    if (rc != LB_OK) break;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = lb_fail(c, LB_ECUDA, "timing a batched launch shape failed");
+      break;
+    }
+    if (ms < best_ms) { best_ms = ms; best = s; }
+  }
+  c->prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LB_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  *shape = best;
+  return LB_OK;
+}
 
 template <int RC>
 static int launch_pass(lb_ctx* c, int prec, bool pass2, int R, const double* d1, const double* d2, double* part,
                        int* nsplit_out) {
   const int64_t Npad = c->Npad;
-  MaskTable* m = nullptr;
-  LB_CHECK(lb_get_mask(c, BT_NTH, BT_TS, &m));
-  const int64_t ntb = m->ntb, ntiles = m->ntiles;
   const int npl = pass2 ? 2 : 1;
   const int64_t nq = Npad * npl * RC;
-  int nsplit = 1;
-  if (prec == LB_FP32) {
+  const bool df = prec != LB_FP32;
+  const void* G = nullptr;
+  const void* Q = nullptr;
+  if (!df) {
     LB_CHECK(lb_ensure(c, c->ws_src, (size_t)nq * sizeof(float)));
     LB_CHECK(lb_ensure(c, c->ws_dlow, (size_t)nq * sizeof(float)));
-    float* Q = (float*)c->ws_src.p;
-    k_packq32<<<lb_div_up(nq, 256), 256, 0, c->stream>>>(c->N, Npad, R, RC, npl, c->w, d1, d2, Q,
+    float* q = (float*)c->ws_src.p;
+    k_packq32<<<lb_div_up(nq, 256), 256, 0, c->stream>>>(c->N, Npad, R, RC, npl, c->w, d1, d2, q,
                                                           (float*)c->ws_dlow.p);
     LB_LAUNCH(c);
-    auto kern = pass2 ? k_farb32<FAR_K2, RC> : k_farb32<FAR_K1, RC>;
-    LB_CHECK(pick_nsplit(c, kern, ntb, ntiles, &nsplit));
-    const int tps = (int)((ntiles + nsplit - 1) / nsplit);
-    ProfScope prof(c, pass2 ? LB_PROF_FAR32_K2 : LB_PROF_FAR32_K1, c->N * c->N * R);
-    kern<<<dim3((unsigned)ntb, (unsigned)nsplit), BT_NTH, 0, c->stream>>>(
-        c->N, c->np, c->pos32, c->nrm32, (const float4*)Q, m->flags, ntiles, c->row_ptr, c->near_patch, tps, part);
-    LB_LAUNCH(c);
+    Q = q;
   } else {
     // geometry planes of the double-float kernels, then the charges
     const size_t geo = 4 * (size_t)Npad * sizeof(float4);
     LB_CHECK(lb_ensure(c, c->ws_src, geo + (size_t)nq * sizeof(float2)));
     LB_CHECK(lb_ensure(c, c->ws_dlow, (size_t)nq * sizeof(float2)));
-    void* G = c->ws_src.p;
-    float2* Q = (float2*)((char*)G + geo);
-    LB_CHECK(lb_pack_df(c, d1, nullptr, G));  // positions and normals; its charge slots are not read
-    k_packqdf<<<lb_div_up(nq, 256), 256, 0, c->stream>>>(c->N, Npad, R, RC, npl, c->w, d1, d2, Q,
+    void* g = c->ws_src.p;
+    float2* q = (float2*)((char*)g + geo);
+    LB_CHECK(lb_pack_df(c, d1, nullptr, g));  // positions and normals; its charge slots are not read
+    k_packqdf<<<lb_div_up(nq, 256), 256, 0, c->stream>>>(c->N, Npad, R, RC, npl, c->w, d1, d2, q,
                                                           (float2*)c->ws_dlow.p);
     LB_LAUNCH(c);
-    auto kern = pass2 ? k_farbdf<FAR_K2, RC> : k_farbdf<FAR_K1, RC>;
-    LB_CHECK(pick_nsplit(c, kern, ntb, ntiles, &nsplit));
-    const int tps = (int)((ntiles + nsplit - 1) / nsplit);
-    ProfScope prof(c, pass2 ? LB_PROF_FARDF_K2 : LB_PROF_FARDF_K1, c->N * c->N * R);
-    kern<<<dim3((unsigned)ntb, (unsigned)nsplit), BT_NTH, 0, c->stream>>>(
-        c->N, Npad, c->np, (const float4*)G, (const float4*)Q, m->flags, ntiles, c->row_ptr, c->near_patch, tps,
-        part);
-    LB_LAUNCH(c);
+    G = g;
+    Q = q;
+  }
+  const int cat = df ? (pass2 ? LB_PROF_FARDF_K2 : LB_PROF_FARDF_K1) : (pass2 ? LB_PROF_FAR32_K2 : LB_PROF_FAR32_K1);
+  int shape = 0;
+  if (pass2) {
+    LB_CHECK((tuned_shape<FAR_K2, RC>(c, df, G, Q, part, &shape)));
+    LB_CHECK((far_any_shape<FAR_K2, RC>(c, shape, df, G, Q, part, nsplit_out, cat, c->N * c->N * R)));
+  } else {
+    LB_CHECK((tuned_shape<FAR_K1, RC>(c, df, G, Q, part, &shape)));
+    LB_CHECK((far_any_shape<FAR_K1, RC>(c, shape, df, G, Q, part, nsplit_out, cat, c->N * c->N * R)));
   }
   lb_pair_counter += c->N * c->N * R;
-  *nsplit_out = nsplit;
   return LB_OK;
 }
 
@@ -636,4 +750,20 @@ int lb_apply_s_batch(lb_ctx* c, int prec, int R, const double* sig, double* out)
   return chunked(
       R, [&](int r0, int k) { return apply_s_chunk<8>(c, prec, k, sig + (int64_t)r0 * N, out + (int64_t)r0 * N); },
       [&](int r0, int k) { return apply_s_chunk<4>(c, prec, k, sig + (int64_t)r0 * N, out + (int64_t)r0 * N); });
+}
+
+// the tuned launch shapes for this context's surface: shapes[8] indexed by
+// precision (0 float32, 1 double-float) * 4 + pass (0 K1, 1 K2) * 2 +
+// (0: 4 densities, 1: 8 densities); -1 where that pass has not run yet
+extern "C" int lb_get_tuning(lb_ctx* c, int* shapes) {
+  if (!c || !shapes) return lb_fail(c, LB_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < 2; ++k)
+      for (int r = 0; r < 2; ++r) {
+        const TuneKey key{c->device, c->N, c->np, r ? 8 : 4, k ? FAR_K2 : FAR_K1, p ? LB_DF64 : LB_FP32};
+        auto it = g_tune.find(key);
+        shapes[p * 4 + k * 2 + r] = it == g_tune.end() ? -1 : it->second;
+      }
+  return LB_OK;
 }

@@ -97,7 +97,8 @@ struct lb_ctx {
 
   // profiling
   int prof_on = 0;
-  std::vector<ProfPending>* capture_prof = nullptr;  // set while a graph is being captured
+  std::vector<ProfPending>* capture_prof = nullptr;  // profiled launches of the graph being captured
+  bool capturing = false;                            // a stream capture is in progress
   int64_t launches = 0;
   std::vector<ProfPending> prof_pending;
   std::vector<cudaEvent_t> ev_pool;

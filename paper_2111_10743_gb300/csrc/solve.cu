@@ -736,7 +736,9 @@ static int lk_capture(lb_ctx* c, Lockstep& L, int prec, const LkAct& act, LkGrap
   LB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   c->stream = c->cap_stream;
   c->capture_prof = &g->prof;
+  c->capturing = true;
   const int rc = lk_iteration(c, L, prec, act);
+  c->capturing = false;
   c->capture_prof = nullptr;
   c->stream = user;
   cudaGraph_t graph = nullptr;

@@ -122,3 +122,29 @@ def test_lockstep_graphs_match_direct_launches(lb, prec):
     assert i2["graph_iterations"] > 0 and np.array_equal(u2, u1)
     far = sum(v["pairs"] for k, v in prof.items() if isinstance(v, dict) and k.startswith("far"))
     assert far == i2["pairs"]
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_batched_launch_shapes(lb, shape, monkeypatch):
+    """Every launch shape the tuner chooses between (threads per block x
+    sources per tile: 128 x 64, 128 x 128, 256 x 64) gives the oracle's A3."""
+    monkeypatch.setenv("GBLB_BATCH_SHAPE", str(shape))
+    name = "torus1920"
+    for prec, tol in (("fp32", 2e-5), ("df64", 1e-12)):
+        ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3,
+                            precision=lb.LB_FP32 if prec == "fp32" else lb.LB_DF64)
+        tau = np.random.default_rng(36).standard_normal((6, d.geo.N))
+        got = ctx.apply_A(tau)
+        ref = d.apply("A3", tau)
+        for r in range(6):
+            assert _rel(got[r], ref[r]) < tol, (prec, r)
+
+
+def test_tuning_recorded(lb):
+    """After batched passes have run, the tuner reports a shape for each
+    (precision, pass, density count) it has seen."""
+    ctx, s, d = ctx_for(lb, "ellipsoid1200", formulation=lb.LB_A3, precision=lb.LB_FP32)
+    ctx.apply_A(np.random.default_rng(37).standard_normal((11, d.geo.N)))   # 8 + 3 densities
+    t = ctx.get_tuning()
+    for k in ("far32_k1_rc8", "far32_k2_rc8", "far32_k1_rc4", "far32_k2_rc4"):
+        assert t[k] in ("128x64", "128x128", "256x64"), (k, t)
