@@ -15,7 +15,9 @@
  *   S'     = -n_x.d/(4 pi r^3)
  *   S''+D' = [3 (n_x.d)((n_x - n_y).d)/r^2 - (1 - n_x.n_y)]/(4 pi r^3)
  *
- * Sources are the N nodes themselves (node j belongs to patch j / np).  A
+ * Sources are the N nodes themselves (node j belongs to patch j / np), or,
+ * for the oversampled far rule of Section 4, Ns given points y_s with their
+ * own normals, weights and densities (point s belongs to patch s / nps).  A
  * plain double loop, parallel over targets with OpenMP.
  */
 #include <math.h>
@@ -23,14 +25,17 @@
 #include <stdlib.h>
 #include <string.h>
 
-int oracle_far_sums(int64_t N, int64_t np_, const double *X, const double *n,
-                    const double *w, const int64_t *near_ptr, const int32_t *near_patch,
-                    int nrhs, const double *sigma, int64_t ntgt, const int64_t *targets,
-                    double *out)
+/* Sources given explicitly: Ns points Y with normals ny, weights wy and
+ * densities sigma_src [nrhs][Ns]; source s lies on patch s / nps.  Targets
+ * are nodes of the surface (X, n, near lists over its patches). */
+int oracle_far_sums_src(int64_t N, const double *X, const double *n, const int64_t *near_ptr,
+                        const int32_t *near_patch, int64_t npatch, int64_t Ns, int64_t nps,
+                        const double *Y, const double *ny, const double *wy, int nrhs,
+                        const double *sigma_src, int64_t ntgt, const int64_t *targets, double *out)
 {
     const double four_pi = 4.0 * 3.14159265358979323846;
-    const int64_t npatch = N / np_;
     int bad = 0;
+    (void)N;
 #pragma omp parallel
     {
         char *is_near = (char *)calloc((size_t)npatch, 1);
@@ -47,10 +52,10 @@ int oracle_far_sums(int64_t N, int64_t np_, const double *X, const double *n,
             memset(acc, 0, sizeof(double) * 4 * (size_t)nrhs);
             const double xi0 = X[3 * i], xi1 = X[3 * i + 1], xi2 = X[3 * i + 2];
             const double nx0 = n[3 * i], nx1 = n[3 * i + 1], nx2 = n[3 * i + 2];
-            for (int64_t j = 0; j < N; ++j) {
-                if (is_near[j / np_]) continue;
-                const double d0 = xi0 - X[3 * j], d1 = xi1 - X[3 * j + 1], d2 = xi2 - X[3 * j + 2];
-                const double ny0 = n[3 * j], ny1 = n[3 * j + 1], ny2 = n[3 * j + 2];
+            for (int64_t j = 0; j < Ns; ++j) {
+                if (is_near[j / nps]) continue;
+                const double d0 = xi0 - Y[3 * j], d1 = xi1 - Y[3 * j + 1], d2 = xi2 - Y[3 * j + 2];
+                const double ny0 = ny[3 * j], ny1 = ny[3 * j + 1], ny2 = ny[3 * j + 2];
                 const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
                 const double r = sqrt(r2);
                 const double g = 1.0 / (four_pi * r);
@@ -63,7 +68,7 @@ int oracle_far_sums(int64_t N, int64_t np_, const double *X, const double *n,
                 const double kSp = -nxd * g3;
                 const double kSD = (3.0 * nxd * (nxd - nyd) / r2 - (1.0 - nxny)) * g3;
                 for (int r_ = 0; r_ < nrhs; ++r_) {
-                    const double q = w[j] * sigma[(int64_t)r_ * N + j];
+                    const double q = wy[j] * sigma_src[(int64_t)r_ * Ns + j];
                     acc[4 * r_ + 0] += kS * q;
                     acc[4 * r_ + 1] += kD * q;
                     acc[4 * r_ + 2] += kSp * q;
@@ -79,4 +84,14 @@ int oracle_far_sums(int64_t N, int64_t np_, const double *X, const double *n,
         free(acc);
     }
     return bad ? -1 : 0;
+}
+
+/* The nodes themselves as sources (the base far rule). */
+int oracle_far_sums(int64_t N, int64_t np_, const double *X, const double *n,
+                    const double *w, const int64_t *near_ptr, const int32_t *near_patch,
+                    int nrhs, const double *sigma, int64_t ntgt, const int64_t *targets,
+                    double *out)
+{
+    return oracle_far_sums_src(N, X, n, near_ptr, near_patch, N / np_, N, np_, X, n, w, nrhs, sigma, ntgt,
+                               targets, out);
 }

@@ -36,13 +36,43 @@ def _load():
             ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_far_sums_src.restype = ctypes.c_int
+        lib.oracle_far_sums_src.argtypes = [
+            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+            ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+            ctypes.c_void_p]
         _lib = lib
     return _lib
 
 
-def far_sums(geo, near_ptr, near_patch, sigma, targets=None) -> np.ndarray:
-    """Far sums of all four kernels: [nrhs, 4, ntargets] (kernel order S, D, S', S''+D')."""
+def far_sums(geo, near_ptr, near_patch, sigma, targets=None, far=None) -> np.ndarray:
+    """Far sums of all four kernels: [nrhs, 4, ntargets] (kernel order S, D, S', S''+D').
+
+    far (a geometry.FarRule) replaces the nodes as sources by the oversampled
+    rule's points, with the densities interpolated to them (Section 4)."""
     lib = _load()
+    if far is not None:
+        sig = np.ascontiguousarray(far.densities(sigma), dtype=np.float64)
+        nrhs = sig.shape[0]
+        if targets is None:
+            targets = np.arange(geo.N, dtype=np.int64)
+        targets = np.ascontiguousarray(targets, dtype=np.int64)
+        X = np.ascontiguousarray(geo.X)
+        n = np.ascontiguousarray(geo.n)
+        Y = np.ascontiguousarray(far.Y)
+        ny = np.ascontiguousarray(far.n)
+        wy = np.ascontiguousarray(far.w)
+        ptr = np.ascontiguousarray(near_ptr, dtype=np.int64)
+        pl = np.ascontiguousarray(near_patch, dtype=np.int32)
+        out = np.zeros((nrhs, 4, len(targets)))
+        rc = lib.oracle_far_sums_src(geo.N, X.ctypes.data, n.ctypes.data, ptr.ctypes.data, pl.ctypes.data,
+                                     geo.npatch, Y.shape[0], far.nps, Y.ctypes.data, ny.ctypes.data,
+                                     wy.ctypes.data, nrhs, sig.ctypes.data, len(targets), targets.ctypes.data,
+                                     out.ctypes.data)
+        if rc != 0:
+            raise MemoryError("oracle far sum could not allocate its work arrays")
+        return out
     sig = np.ascontiguousarray(np.atleast_2d(sigma), dtype=np.float64)
     nrhs = sig.shape[0]
     if targets is None:

@@ -136,3 +136,38 @@ def surface_divergence(geo: Geometry, F: np.ndarray) -> np.ndarray:
     P2 = (geo.J * F2).reshape(geo.npatch, geo.np_)
     d = (np.einsum("ab,pb->pa", geo.basis.Du, P1) + np.einsum("ab,pb->pa", geo.basis.Dv, P2))
     return d.reshape(geo.N) / geo.J
+
+
+@dataclass
+class FarRule:
+    """Oversampled far-field sources (Section 4): on every patch, the patch
+    interpolants of X, X_u and X_v evaluated at the nodes of a finer rule
+    (uv_o, w_o) on T0.  Source s lies on patch s // nps; its normal is
+    X_u x X_v / |X_u x X_v| and its weight w_o |X_u x X_v| of the interpolated
+    tangents, and its density the interpolant of the nodal density."""
+    nps: int
+    I: np.ndarray   # [n_o, n_p] base-rule Lagrange basis at the fine nodes
+    Y: np.ndarray   # [npatch * n_o, 3]
+    n: np.ndarray   # [npatch * n_o, 3]
+    w: np.ndarray   # [npatch * n_o]
+
+    def densities(self, sigma: np.ndarray) -> np.ndarray:
+        """Nodal densities [nrhs, N] -> source densities [nrhs, npatch * n_o]."""
+        sig = np.atleast_2d(sigma)
+        npatch = self.Y.shape[0] // self.nps
+        s = sig.reshape(sig.shape[0], npatch, self.I.shape[1])
+        return np.einsum("qb,rpb->rpq", self.I, s).reshape(sig.shape[0], -1)
+
+
+def oversample(geo: Geometry, uv_o, w_o) -> FarRule:
+    uv_o = np.asarray(uv_o, dtype=np.float64)
+    w_o = np.asarray(w_o, dtype=np.float64)
+    I = geo.basis.lagrange(uv_o[:, 0], uv_o[:, 1])
+    shape = (geo.npatch, geo.np_, 3)
+    Y = np.einsum("qb,pbk->pqk", I, geo.X.reshape(shape)).reshape(-1, 3)
+    Xu = np.einsum("qb,pbk->pqk", I, geo.Xu.reshape(shape)).reshape(-1, 3)
+    Xv = np.einsum("qb,pbk->pqk", I, geo.Xv.reshape(shape)).reshape(-1, 3)
+    c = np.cross(Xu, Xv)
+    J = np.linalg.norm(c, axis=1)
+    w = np.tile(w_o, geo.npatch) * J
+    return FarRule(len(w_o), I, Y, c / J[:, None], w)

@@ -38,6 +38,7 @@ class Discretisation:
     vals: np.ndarray        # [nnzb, 4, n_p] near-field weights
     eta: float
     eps_q: float
+    far: object = None      # geometry.FarRule: oversampled far-field sources (Section 4), or None
 
     def near_apply(self, sigma: np.ndarray, targets=None) -> np.ndarray:
         """Correction sums [nrhs, 4, ntargets] from the block CSR."""
@@ -55,7 +56,7 @@ class Discretisation:
 
     def potentials(self, sigma: np.ndarray, targets=None) -> np.ndarray:
         """All four discretised potentials: [nrhs, 4, ntargets]."""
-        return farsum.far_sums(self.geo, self.near_ptr, self.near_patch, sigma, targets) + \
+        return farsum.far_sums(self.geo, self.near_ptr, self.near_patch, sigma, targets, far=self.far) + \
             self.near_apply(sigma, targets)
 
     def wmean(self, f: np.ndarray) -> np.ndarray:

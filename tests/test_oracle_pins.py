@@ -169,6 +169,28 @@ def test_far_sums_unit_sphere_identities(sphere):
     assert np.abs(Ft - F[:, :, t]).max() == 0.0
 
 
+def test_oversampled_far_rule(sphere):
+    """The oversampled far rule (Section 4): interpolating to the base rule
+    itself reproduces the plain far sums; on a finer rule the interpolated
+    unit sphere keeps its radius, radial normals and area 4 pi to the
+    interpolation error of degree-6 patches."""
+    from oracle.geometry import oversample
+    from workloads.nodes import node_rule
+    g = sphere.geo
+    sig = np.random.default_rng(8).standard_normal((2, g.N))
+    base = farsum.far_sums(g, sphere.near_ptr, sphere.near_patch, sig)
+    ident = farsum.far_sums(g, sphere.near_ptr, sphere.near_patch, sig, far=oversample(g, g.basis.uv, g.wref))
+    assert np.abs(ident - base).max() < 1e-13 * np.abs(base).max()
+    f = oversample(g, *node_rule(8))
+    r = np.linalg.norm(f.Y, axis=1)
+    assert np.abs(r - 1.0).max() < 2e-6
+    assert np.abs(f.n - f.Y / r[:, None]).max() < 5e-5
+    assert abs(f.w.sum() - 4.0 * np.pi) < 2e-5
+    # the densities are the patch interpolants: a linear function is reproduced exactly
+    lin = f.densities(g.X[:, 0] + 2.0 * g.X[:, 2])[0]
+    assert np.abs(lin - (f.Y[:, 0] + 2.0 * f.Y[:, 2])).max() < 1e-13
+
+
 # --- potentials: far + near (Sections 3, 4) --------------------------------
 
 @pytest.mark.parametrize("l", [0, 1, 2, 3, 4])
