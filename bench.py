@@ -69,6 +69,17 @@ def _dist():
     return ws, rank, local
 
 
+def worst_over_ranks(values, device="cpu"):
+    """Elementwise maximum of per-rank timings over all ranks (every replica
+    times its own solves; the slowest one sets the whole job's time)."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
 class ClockSampler:
     """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
 
@@ -233,10 +244,7 @@ def run_ours(args):
     e2e_pairs = info_e["pairs"]
 
     # worst rank
-    tot = torch.tensor([ms, sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(tot, op=torch.distributed.ReduceOp.MAX)
-    ms_max, e2e_max = float(tot[0]), float(tot[1])
+    ms_max, e2e_max = worst_over_ranks([ms, sum(e2e_ms) / len(e2e_ms)], device="cuda")
     if rank != 0:
         return
     ms_step = ms_max / args.steps
