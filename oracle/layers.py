@@ -24,7 +24,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import farsum
-from .geometry import Geometry, near_lists
+from .geometry import Geometry, near_lists, surface_gradient
 from .quadrature import build_corrections
 
 K_S, K_D, K_SP, K_SD = 0, 1, 2, 3
@@ -85,7 +85,29 @@ class Discretisation:
         q2 = self.potentials(mu2)
         return -0.25 * tau + q1[:, K_D] + q2[:, K_S]
 
+    def apply_A1(self, tau: np.ndarray) -> np.ndarray:
+        """A1 = div S grad_Gamma S + S W S (Section 4.1, eq. ie-dis0), applied
+        right to left: s = S[tau]; mu = grad_Gamma s; the divergence of the
+        vector single layer of mu, sum_l d_l S[mu_l], with the principal-value
+        gradient d_l S[sigma] = n_l S'[sigma] + (grad_Gamma S[sigma])_l; plus
+        W[s] S[1]."""
+        tau = np.atleast_2d(tau)
+        geo = self.geo
+        nr = tau.shape[0]
+        s = self.S(tau)                                        # [r, N]
+        mu = surface_gradient(geo, s.T)                        # [N, r, 3]
+        P = self.potentials(mu.transpose(1, 2, 0).reshape(nr * 3, geo.N))   # [r*3, 4, N]
+        g = surface_gradient(geo, P[:, K_S].T).reshape(geo.N, nr, 3, 3)     # [N, r, l, 3]
+        Sp = P[:, K_SP].reshape(nr, 3, geo.N)
+        out = np.zeros_like(tau)
+        for l in range(3):
+            out += geo.n[None, :, l] * Sp[:, l] + g[:, :, l, l].T
+        one = self.S(np.ones(geo.N))[0]
+        return out + self.wmean(s)[:, None] * one[None, :]
+
     def apply(self, formulation: str, tau):
+        if formulation == "A1":
+            return self.apply_A1(tau)
         return self.apply_A3(tau) if formulation == "A3" else self.apply_A2(tau)
 
     def S(self, sigma):
@@ -97,7 +119,7 @@ class Discretisation:
 
     def rhs(self, formulation: str, f):
         f0 = self.project_mean_zero(f)
-        return f0 if formulation == "A3" else self.S(f0)
+        return f0 if formulation == "A3" else self.S(f0)   # A1 and A2 take S[f]
 
     def solution(self, formulation: str, sigma):
         s = self.S(sigma)

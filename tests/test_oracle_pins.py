@@ -212,6 +212,41 @@ def test_sphere_spectrum_of_operators(sphere, l, form):
     assert np.abs(Af - gold * f).max() < 2e-3 * np.abs(f).max()
 
 
+@pytest.mark.parametrize("l", [0, 1, 2, 3, 4])
+def test_sphere_spectrum_of_A1(sphere, l):
+    """A1 = S (Delta + W) S (Section 4.1): eigenvalue -l(l+1)/(2l+1)^2 on
+    Y_l (l >= 1) and 1 on constants on the unit sphere.  The surface
+    derivatives are nodal, so the error grows with l."""
+    f = _harmonic(l, sphere.geo.X)
+    lam = 1.0 if l == 0 else -l * (l + 1) / (2 * l + 1) ** 2
+    err = np.abs(sphere.apply_A1(f)[0] - lam * f).max() / np.abs(lam * f).max()
+    assert err < (1e-3 if l <= 1 else 1e-2), err
+
+
+def test_numerical_second_kindness():
+    """Section 6.2 on the sphere, order-3 patches, N = 200 and 800.
+    - A2 and A3 have an explicit identity term: their singular values cluster
+      at 1/4 and their smallest one does not change under refinement.
+    - A1 has none.  With surface gradients taken by nodal differentiation
+      inside each patch it has an exact null space: the densities whose
+      S[tau] is constant on every patch, minus the global constant that W
+      lifts, so npatch - 1 zero singular values."""
+    from oracle.gmres import dense_matrix
+    smin = {}
+    for lev in (0, 1):
+        s = S.icosphere(lev, 3)
+        d = discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0, eps_q=5e-8, workers=WORKERS)
+        for form in ("A1", "A2", "A3"):
+            sv = np.linalg.svd(dense_matrix(lambda x: d.apply(form, x), s.N), compute_uv=False)
+            if form == "A1":
+                assert int(np.sum(sv < 1e-10 * sv.max())) == s.npatch - 1
+            else:
+                assert sv.min() > 0.2 and abs(np.median(sv) - 0.25) < 0.01
+                smin[(form, lev)] = sv.min()
+    for form in ("A2", "A3"):
+        assert abs(smin[(form, 1)] / smin[(form, 0)] - 1.0) < 0.05
+
+
 def test_ellipsoid_gauss_green_adjoint(ellipsoid):
     g = ellipsoid.geo
     one = np.ones(g.N)
