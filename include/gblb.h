@@ -58,6 +58,8 @@ extern "C" {
                               error-free transformations, about 1e-14 relative */
 
 /* integral-equation formulation (Section 4, Table 2) */
+#define LB_A1 1   /* u = S[sigma]:   div S grad_Gamma S [sigma] + SWS[sigma] = S[f] (Section 4.1,
+                     eq. ie-dis0; not second kind: the comparison case of Section 6.2) */
 #define LB_A2 2   /* u = S[sigma]:   -sigma/4 + D^2 - S(S''+D'+2HS') + SWS = S[f]  */
 #define LB_A3 3   /* u = S^2[sigma]: -sigma/4 + S'^2 - (S''+D'+2HS')S + WS^2 = f    */
 
@@ -74,7 +76,7 @@ typedef struct {
   double eps_quad;      /* near-field quadrature tolerance (Section 6: epsilon); default 1e-12 */
   double near_factor;   /* eta: patch P is near node x when |x - c_P| < eta * R_P; default 2 */
   int precision;        /* LB_FP64, LB_FP32, LB_FP32_REFINED or LB_DF64; default LB_FP64 */
-  int formulation;      /* LB_A3 or LB_A2; default LB_A3 */
+  int formulation;      /* LB_A3, LB_A2 or LB_A1; default LB_A3 */
   int max_iter;         /* GMRES iteration cap (Section 6 caps at 100); default 100 */
   double tol;           /* relative residual target |b - A x| / |b|; default 1e-10 */
   double inner_tol;     /* LB_FP32_REFINED: inner GMRES relative tolerance; default 1e-5 */

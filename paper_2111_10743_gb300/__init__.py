@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgblb.so")
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENOTCONVERGED, LB_ETIMEOUT, LB_EGEOM, LB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 LB_FP64, LB_FP32, LB_FP32_REFINED, LB_DF64 = 0, 1, 2, 3
-LB_A2, LB_A3 = 2, 3
+LB_A1, LB_A2, LB_A3 = 1, 2, 3
 LB_K_S, LB_K_D, LB_K_SP, LB_K_SPPDP = 0, 1, 2, 3
 NKERNELS = 4
 _STATUS = {0: "LB_OK", -1: "LB_EINVAL", -2: "LB_ENOMEM", -3: "LB_ECUDA", -4: "LB_ENOTCONVERGED",

@@ -186,7 +186,8 @@ static int check_params(lb_ctx* c, const lb_params* p) {
   if (!(p->near_factor > 1.0 && p->near_factor < 1e3))
     return lb_fail(c, LB_EINVAL, "near_factor must be in (1, 1000): the own patch must be near");
   if (p->precision < LB_FP64 || p->precision > LB_DF64) return lb_fail(c, LB_EINVAL, "bad precision");
-  if (p->formulation != LB_A2 && p->formulation != LB_A3) return lb_fail(c, LB_EINVAL, "bad formulation");
+  if (p->formulation != LB_A1 && p->formulation != LB_A2 && p->formulation != LB_A3)
+    return lb_fail(c, LB_EINVAL, "bad formulation");
   if (p->max_iter < 1 || p->max_iter > 1000) return lb_fail(c, LB_EINVAL, "max_iter must be in [1,1000]");
   if (!(p->tol > 0 && p->tol < 1)) return lb_fail(c, LB_EINVAL, "tol must be in (0,1)");
   if (!(p->inner_tol > 0 && p->inner_tol < 1)) return lb_fail(c, LB_EINVAL, "inner_tol must be in (0,1)");
@@ -239,6 +240,8 @@ static void free_geometry(lb_ctx* c) {
 static void free_near(lb_ctx* c) {
   lb_free(&c->row_ptr); lb_free(&c->near_patch); lb_free(&c->vals);
   lb_free(&c->vals_hi); lb_free(&c->vals_lo);
+  lb_free(&c->phi0);
+  c->phi0_prec = -1;
   for (auto& m : c->masks) lb_free(&m.flags);
   c->masks.clear();
   c->have_near = c->have_corr = false;
@@ -252,7 +255,7 @@ extern "C" int lb_destroy(lb_ctx* c) {
   free_geometry(c);
   free_near(c);
   for (DevBuf* b : {&c->ws_part, &c->ws_pot, &c->ws_src, &c->ws_vec, &c->ws_red, &c->ws_stage_in,
-                    &c->ws_stage_out, &c->ws_gm, &c->ws_quad, &c->ws_bpot, &c->ws_bgm, &c->ws_bvec, &c->ws_dlow})
+                    &c->ws_stage_out, &c->ws_gm, &c->ws_quad, &c->ws_bpot, &c->ws_bgm, &c->ws_bvec, &c->ws_dlow, &c->ws_a1})
     if (b->p) cudaFree(b->p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -607,6 +610,8 @@ extern "C" int lb_load_corrections(lb_ctx* c, int64_t nnzb, const int64_t* row_p
   LB_CHECK(lb_alloc(c, &c->near_patch, nnzb));
   lb_free(&c->vals_hi);
   lb_free(&c->vals_lo);
+  lb_free(&c->phi0);
+  c->phi0_prec = -1;
   LB_CHECK(lb_alloc(c, &c->vals, nnzb * LB_NKERNELS * c->np));
   LB_CUDA(c, cudaMemcpyAsync(c->row_ptr, row_ptr, (N + 1) * sizeof(int64_t), cudaMemcpyDefault, c->stream));
   LB_CUDA(c, cudaMemcpyAsync(c->near_patch, patch, nnzb * sizeof(int32_t), cudaMemcpyDefault, c->stream));

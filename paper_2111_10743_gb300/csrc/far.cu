@@ -839,6 +839,7 @@ int lb_potentials(lb_ctx* c, int prec, const double* sigma, double* pot, unsigne
 }
 
 int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double* out) {
+  if (formulation == LB_A1) return lb_apply_a1(c, prec, tau, out);
   const int64_t N = c->N;
   LB_CHECK(lb_ensure(c, c->ws_pot, (size_t)(8 * N) * sizeof(double)));
   double* pot = (double*)c->ws_pot.p;   // [4][N] pass-1 potentials, then pass-2

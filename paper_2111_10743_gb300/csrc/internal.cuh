@@ -110,6 +110,9 @@ struct lb_ctx {
   DevBuf ws_part, ws_pot, ws_src, ws_vec, ws_red, ws_stage_in, ws_stage_out, ws_gm, ws_quad;
   DevBuf ws_bpot, ws_bgm, ws_bvec;  // batched applies and the lockstep solver
   DevBuf ws_dlow;                   // float32 / double-float copies of correction densities
+  DevBuf ws_a1;                     // A1 apply: surface gradients and vector single layers
+  double* phi0 = nullptr;           // S[1] for A1's S W S term, in pair precision phi0_prec
+  int phi0_prec = -1;
   double* host_pinned = nullptr;  // pinned scalars for GMRES control [LB_PINNED_DOUBLES]
 };
 
@@ -182,6 +185,8 @@ int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* s
 int lb_potentials(lb_ctx* c, int prec, const double* sigma, double* pot, unsigned which);
 // apply the formulation operator to one vector (device in, device out)
 int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double* out);
+// A1 applied to one density (device in, device out); leaves S[tau] in ws_pot
+int lb_apply_a1(lb_ctx* c, int prec, const double* tau, double* out);
 int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out);
 // float32 hi / lo copies of the correction weights (no-op when present)
 int lb_lowp_vals(lb_ctx* c);

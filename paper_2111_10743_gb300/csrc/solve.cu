@@ -1035,7 +1035,7 @@ static int solve_batch(lb_ctx* c, int nrhs, const double* f, double* u, lb_solve
     double removed = 0;
     LB_CHECK(project_mean_zero(c, fr, fb, &removed));
     if (info && r == 0) info->removed_mean = removed;
-    if (p.formulation == LB_A2) {  // b = S[f]
+    if (p.formulation != LB_A3) {  // A1, A2: b = S[f]
       LB_CHECK(apply_S_dev(c, post, fb, tmp));
       LB_CUDA(c, cudaMemcpyAsync(fb, tmp, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     }
@@ -1184,6 +1184,89 @@ extern "C" int lb_apply_gradS(lb_ctx* c, int nrhs, const double* sigma, double* 
     LB_LAUNCH(c);
   }
   return lb_stage_out_finish(c, out, dout, nrhs * 3 * N * sizeof(double));
+}
+
+// ---------------------------------------------------------------------------
+// A1 = div S grad_Gamma S + S W S (Section 4.1, eq. ie-dis0), applied right
+// to left: s = S[tau]; mu = grad_Gamma s by nodal differentiation; the vector
+// single layer of mu and its divergence sum_l d_l S[mu_l], each d_l S[sigma]
+// the principal-value gradient n_l S'[sigma] + (grad_Gamma S[sigma])_l; plus
+// W[s] S[1], with S[1] computed once per pair precision.
+
+// g [N][3] -> out [3][N]
+__global__ void k_vec_split(int64_t N, const double* __restrict__ g, double* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < 3; ++k) out[k * N + i] = g[3 * i + k];
+}
+
+// div (+)= component l of the gradient g [N][3]
+__global__ void k_a1_acc(int64_t N, int l, const double* __restrict__ g, double* __restrict__ div) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    div[i] = (l == 0 ? 0.0 : div[i]) + g[3 * i + l];
+}
+
+// out = div + (sum of the w s partials / area) S[1]
+__global__ void k_a1_final(int64_t N, const double* __restrict__ div, const double* __restrict__ phi0,
+                           const double* __restrict__ partial, int npart, double area, double* __restrict__ out) {
+  __shared__ double eta;
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < npart; ++k) s += partial[k];
+    eta = s / area;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = div[i] + eta * phi0[i];
+}
+
+__global__ void k_fill(int64_t N, double v, double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+int lb_apply_a1(lb_ctx* c, int prec, const double* tau, double* out) {
+  const int64_t N = c->N;
+  const unsigned nb = vec_blocks(c), gb = lb_div_up(N, 128);
+  LB_CHECK(lb_ensure(c, c->ws_pot, (size_t)(8 * N) * sizeof(double)));
+  LB_CHECK(lb_ensure(c, c->ws_a1, (size_t)(15 * N + GM_RB) * sizeof(double)));
+  double* pot = (double*)c->ws_pot.p;      // [4][N]: S[tau] at K_S
+  double* a = (double*)c->ws_a1.p;
+  double* mu = a;                          // [N][3]
+  double* mus = mu + 3 * N;                // [3][N]
+  double* potl = mus + 3 * N;              // [4][N]
+  double* grad = potl + 4 * N;             // [N][3]
+  double* div = grad + 3 * N;              // [N]
+  double* tmp = div + N;                   // [N]
+  double* partial = tmp + N;               // [GM_RB]
+  if (!c->phi0 || c->phi0_prec != prec) {  // S[1]
+    LB_CHECK(lb_alloc(c, &c->phi0, (size_t)N));
+    k_fill<<<nb, 256, 0, c->stream>>>(N, 1.0, tmp);
+    LB_LAUNCH(c);
+    LB_CHECK(lb_potentials(c, prec, tmp, potl, 1u << LB_K_S));
+    LB_CUDA(c, cudaMemcpyAsync(c->phi0, potl + LB_K_S * N, N * sizeof(double), cudaMemcpyDeviceToDevice,
+                               c->stream));
+    c->phi0_prec = prec;
+  }
+  LB_CHECK(lb_potentials(c, prec, tau, pot, 1u << LB_K_S));
+  const double* s = pot + LB_K_S * N;
+  k_surf_grad<<<gb, 128, 0, c->stream>>>(N, c->np, s, c->dDu, c->dDv, c->ginv, c->Xu, c->Xv, nullptr, c->nrm, mu);
+  LB_LAUNCH(c);
+  k_vec_split<<<nb, 256, 0, c->stream>>>(N, mu, mus);
+  LB_LAUNCH(c);
+  for (int l = 0; l < 3; ++l) {
+    LB_CHECK(lb_potentials(c, prec, mus + l * N, potl, (1u << LB_K_S) | (1u << LB_K_SP)));
+    k_surf_grad<<<gb, 128, 0, c->stream>>>(N, c->np, potl + LB_K_S * N, c->dDu, c->dDv, c->ginv, c->Xu, c->Xv,
+                                            potl + LB_K_SP * N, c->nrm, grad);
+    LB_LAUNCH(c);
+    k_a1_acc<<<nb, 256, 0, c->stream>>>(N, l, grad, div);
+    LB_LAUNCH(c);
+  }
+  k_multidot<<<GM_RB, 256, 0, c->stream>>>(N, 1, s, N, c->w, partial);
+  LB_LAUNCH(c);
+  k_a1_final<<<nb, 256, 0, c->stream>>>(N, div, c->phi0, partial, GM_RB, c->area, out);
+  LB_LAUNCH(c);
+  if (prec == LB_FP32) ++lb_apply32_counter; else ++lb_apply64_counter;
+  return LB_OK;
 }
 
 // H = F - grad a - n x grad b, and n x H

@@ -291,3 +291,15 @@ def test_twisted_torus_against_paper_table(lb):
     # discretisation errors: same order of magnitude as the paper's
     assert row[3] / 2 < l2(ctx.surface_div(H[0][None])[0]) < 2 * row[3]
     assert l2(ctx.surface_div(H[1][None])[0]) < 2 * row[4]
+
+
+@pytest.mark.parametrize("name", ["sphere300", "ellipsoid1200"])
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+def test_operator_A1(lb, name, prec):
+    """A1 = div S grad_Gamma S + S W S (Section 4.1) against the oracle."""
+    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A1,
+                        precision=lb.LB_FP64 if prec == "fp64" else lb.LB_DF64)
+    tau = np.random.default_rng(38).standard_normal((2, d.geo.N))
+    # two nodal differentiations amplify the pair sums' rounding (~1e-15 in
+    # float64, ~1e-14 in double-float) by about 1e3
+    assert _rel(ctx.apply_A(tau), d.apply("A1", tau)) < (1e-11 if prec == "fp64" else 1e-10)
