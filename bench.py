@@ -145,19 +145,26 @@ def _peaks():
         return {}
 
 
-def _traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if still current."""
+def source_digest(name: str) -> str:
+    """First 16 hex digits of the SHA-256 of a CUDA source file of the library."""
+    src = os.path.join(ROOT, "paper_2111_10743_gb300", "csrc", name)
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def _traffic(kernel: str, n_nodes: int):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.json (an ncu
+    capture of dram__bytes_read.sum + dram__bytes_write.sum), or None when the
+    kernel's source has changed since.  The capture is on a smaller surface;
+    the sources and targets stay in L2, so DRAM traffic grows with the node
+    count N, not with the N^2 pairs, and is scaled by N."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        t = json.load(open(path))
+        ent = json.load(open(path)).get(kernel)
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2111_10743_gb300", "csrc", "far.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    ent = t.get(kernel)
-    if not ent or ent.get("far_cu_sha256") != digest:
+    if not ent or not ent.get("source") or ent.get("source_sha256") != source_digest(ent["source"]):
         return None
-    return ent.get("dram_bytes_per_launch")
+    return int(ent["dram_bytes_per_launch"] * n_nodes / ent["captured_n"])
 
 
 def run_ours(args):
@@ -285,7 +292,7 @@ def run_ours(args):
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 3),
                     "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "traffic": _traffic(dom), "peak_source": note,
+                    "traffic": _traffic(kname, s.N), "peak_source": note,
                     "launch_ms": round(per_launch_ms, 4), "share_of_step": round(cats[dom]["ms"] / ms, 4)}
     kernels = {k: {"ms_per_step": round(v["ms"] / args.steps, 3), "calls_per_step": v["calls"] / args.steps,
                    **({"gpairs_per_step": round(v["pairs"] / args.steps / 1e9, 3)} if v.get("pairs") else {})}
