@@ -95,6 +95,8 @@ def _load():
         "lb_solve_lb": [P, ctypes.c_int, P, P, P], "lb_harmonic_fields": [P, ctypes.c_int, P, P, P],
         "lb_surface_div": [P, ctypes.c_int, P, P],
         "lb_set_profiling": [P, ctypes.c_int], "lb_get_profile": [P, P], "lb_get_tuning": [P, P],
+        "lb_apply_St": [P, ctypes.c_int, P, P], "lb_apply_At": [P, ctypes.c_int, P, P],
+        "lb_solve_lb_adjoint": [P, ctypes.c_int, P, P, P],
         "lb_far_sums_noalloc": [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
@@ -317,6 +319,25 @@ class Context:
                     allow=(LB_ENOTCONVERGED,) if allow_unconverged else ())
         return res, info.as_dict()
 
+    def apply_St(self, y, out=None):
+        """S^T y (the transpose of the discrete single-layer matrix)."""
+        return self._apply(_lib.lb_apply_St, y, out)
+
+    def apply_At(self, y, out=None):
+        """A3^T y (the transpose of the discrete A3 operator)."""
+        return self._apply(_lib.lb_apply_At, y, out)
+
+    def solve_lb_adjoint(self, gu, out=None, allow_unconverged=False):
+        """Gradient with respect to f of a loss whose gradient with respect
+        to u = solve_lb(f) is gu (A3 formulation)."""
+        nrhs = self._nrhs(gu)
+        p, keep = _ptr(gu, np.float64)
+        o, res = _out(out, np.float64, (nrhs, self.N))
+        info = lb_solve_info()
+        self._check(_lib.lb_solve_lb_adjoint(self._h, nrhs, p, o, ctypes.byref(info)),
+                    allow=(LB_ENOTCONVERGED,) if allow_unconverged else ())
+        return res, info.as_dict()
+
     def harmonic_fields(self, F, out=None):
         nF = self._nrhs(F, 3)
         p, keep = _ptr(F, np.float64)
@@ -324,3 +345,56 @@ class Context:
         info = lb_solve_info()
         self._check(_lib.lb_harmonic_fields(self._h, nF, p, o, ctypes.byref(info)))
         return res, info.as_dict()
+
+
+# --- autograd ---------------------------------------------------------------
+def _torch_fns():
+    import torch
+
+    class SolveLB(torch.autograd.Function):
+        """u = solve_lb(f) with its density gradient g_f = P^T A3^-T S^T S^T g_u.
+
+        f: float64 CUDA tensor [nrhs, N]; ctx_lb: a Context with the A3
+        formulation and corrections.  The backward pass is the library's
+        adjoint solve (transposed applies and GMRES on A3^T)."""
+
+        @staticmethod
+        def forward(ctx, f, ctx_lb):
+            u = torch.empty_like(f)
+            ctx_lb.solve_lb(f.detach().contiguous(), out=u)
+            ctx.ctx_lb = ctx_lb
+            return u
+
+        @staticmethod
+        def backward(ctx, gu):
+            gf = torch.empty_like(gu)
+            ctx.ctx_lb.solve_lb_adjoint(gu.contiguous(), out=gf)
+            return gf, None
+
+    class ApplyA(torch.autograd.Function):
+        """y = A3 tau with gradient A3^T g_y."""
+
+        @staticmethod
+        def forward(ctx, tau, ctx_lb):
+            y = torch.empty_like(tau)
+            ctx_lb.apply_A(tau.detach().contiguous(), out=y)
+            ctx.ctx_lb = ctx_lb
+            return y
+
+        @staticmethod
+        def backward(ctx, gy):
+            gt = torch.empty_like(gy)
+            ctx.ctx_lb.apply_At(gy.contiguous(), out=gt)
+            return gt, None
+
+    return SolveLB, ApplyA
+
+
+def solve_lb_autograd(f, ctx_lb):
+    """Differentiable mean-zero Laplace-Beltrami solve (A3): u = solve(f)."""
+    return _torch_fns()[0].apply(f, ctx_lb)
+
+
+def apply_A_autograd(tau, ctx_lb):
+    """Differentiable A3 apply."""
+    return _torch_fns()[1].apply(tau, ctx_lb)

@@ -237,7 +237,14 @@ static void free_geometry(lb_ctx* c) {
   c->have_geom = false;
 }
 
+void lb_free_transpose(lb_ctx* c) {
+  lb_free(&c->tptr); lb_free(&c->trow); lb_free(&c->tblk); lb_free(&c->tmask); lb_free(&c->tflag);
+  lb_free(&c->v0);
+  c->have_trans = false;
+}
+
 static void free_near(lb_ctx* c) {
+  lb_free_transpose(c);
   lb_free(&c->row_ptr); lb_free(&c->near_patch); lb_free(&c->vals);
   lb_free(&c->vals_hi); lb_free(&c->vals_lo);
   lb_free(&c->phi0);
@@ -255,7 +262,8 @@ extern "C" int lb_destroy(lb_ctx* c) {
   free_geometry(c);
   free_near(c);
   for (DevBuf* b : {&c->ws_part, &c->ws_pot, &c->ws_src, &c->ws_vec, &c->ws_red, &c->ws_stage_in,
-                    &c->ws_stage_out, &c->ws_gm, &c->ws_quad, &c->ws_bpot, &c->ws_bgm, &c->ws_bvec, &c->ws_dlow, &c->ws_a1})
+                    &c->ws_stage_out, &c->ws_gm, &c->ws_quad, &c->ws_bpot, &c->ws_bgm, &c->ws_bvec, &c->ws_dlow, &c->ws_a1,
+                    &c->ws_adj})
     if (b->p) cudaFree(b->p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -612,6 +620,7 @@ extern "C" int lb_load_corrections(lb_ctx* c, int64_t nnzb, const int64_t* row_p
   lb_free(&c->vals_lo);
   lb_free(&c->phi0);
   c->phi0_prec = -1;
+  lb_free_transpose(c);
   LB_CHECK(lb_alloc(c, &c->vals, nnzb * LB_NKERNELS * c->np));
   LB_CUDA(c, cudaMemcpyAsync(c->row_ptr, row_ptr, (N + 1) * sizeof(int64_t), cudaMemcpyDefault, c->stream));
   LB_CUDA(c, cudaMemcpyAsync(c->near_patch, patch, nnzb * sizeof(int32_t), cudaMemcpyDefault, c->stream));

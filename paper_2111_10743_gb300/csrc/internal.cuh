@@ -93,6 +93,16 @@ struct lb_ctx {
   float* vals_hi = nullptr;     // [nnzb][4][np] float32 copy (double-float hi part), made on first use
   float* vals_lo = nullptr;     // [nnzb][4][np] double-float lo part
   std::vector<MaskTable> masks;
+  // transposed near structure (adjoint applies), built on first use
+  bool have_trans = false;
+  int64_t* tptr = nullptr;                // [npatch+1] per target patch
+  int32_t* trow = nullptr;                // [nnzb] rows i with the patch in Near(i), ascending
+  int64_t* tblk = nullptr;                // [nnzb] their correction blocks
+  unsigned long long* tmask = nullptr;    // [npatch][Npad/64] masked sources per 64-source tile
+  uint8_t* tflag = nullptr;               // [target blocks][tiles]
+  int64_t t_ntiles = 0, t_ntb = 0;
+  double* v0 = nullptr;                   // S^T S^T w
+  bool adjoint = false;                   // GMRES applies A3^T
   std::map<const void*, int> occupancy;  // resident blocks per SM, per kernel (queried once)
 
   // profiling
@@ -111,6 +121,7 @@ struct lb_ctx {
   DevBuf ws_bpot, ws_bgm, ws_bvec;  // batched applies and the lockstep solver
   DevBuf ws_dlow;                   // float32 / double-float copies of correction densities
   DevBuf ws_a1;                     // A1 apply: surface gradients and vector single layers
+  DevBuf ws_adj;                    // transposed applies
   double* phi0 = nullptr;           // S[1] for A1's S W S term, in pair precision phi0_prec
   int phi0_prec = -1;
   double* host_pinned = nullptr;  // pinned scalars for GMRES control [LB_PINNED_DOUBLES]
@@ -187,6 +198,11 @@ int lb_potentials(lb_ctx* c, int prec, const double* sigma, double* pot, unsigne
 int lb_apply_op(lb_ctx* c, int formulation, int prec, const double* tau, double* out);
 // A1 applied to one density (device in, device out); leaves S[tau] in ws_pot
 int lb_apply_a1(lb_ctx* c, int prec, const double* tau, double* out);
+// transposes (float64): A3^T y, S^T y (device in, device out)
+int lb_apply_a3t(lb_ctx* c, const double* y, double* out);
+int lb_apply_st_dev(lb_ctx* c, const double* y, double* out);
+int lb_build_transpose(lb_ctx* c);
+void lb_free_transpose(lb_ctx* c);
 int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out);
 // float32 hi / lo copies of the correction weights (no-op when present)
 int lb_lowp_vals(lb_ctx* c);

@@ -360,6 +360,7 @@ extern "C" int lb_build_corrections(lb_ctx* c) {
   lb_free(&c->vals_lo);
   lb_free(&c->phi0);
   c->phi0_prec = -1;
+  lb_free_transpose(c);
   LB_CHECK(lb_alloc(c, &c->vals, (size_t)c->nnzb * LB_NKERNELS * np));
   LB_CHECK(lb_ensure(c, c->ws_quad, (size_t)(3 * c->npatch * np + 16) * sizeof(double)));
   double* cX = (double*)c->ws_quad.p;

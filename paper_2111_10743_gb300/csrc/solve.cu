@@ -253,7 +253,8 @@ static int gmres(lb_ctx* c, int prec, const double* b, double* x, double tol, in
   double r = 1.0;
   for (int j = 0; j < max_iter; ++j) {
     const double* vj = G.V + (int64_t)j * N;
-    LB_CHECK(lb_apply_op(c, c->params.formulation, prec, vj, G.w));
+    if (c->adjoint) LB_CHECK(lb_apply_a3t(c, vj, G.w));
+    else LB_CHECK(lb_apply_op(c, c->params.formulation, prec, vj, G.w));
     LB_CHECK(arnoldi_step(c, G, j, beta));
     LB_CHECK(read_scalar(c, G.scal, &r));
     if (hist) hist->push_back(r);
@@ -1333,5 +1334,97 @@ extern "C" int lb_harmonic_fields(lb_ctx* c, int nF, const double* F, double* H,
   if (rc != LB_OK) return rc;
   LB_CHECK(lb_stage_out_finish(c, H, dH, 2 * nF * 3 * N * sizeof(double)));
   if (info && !info->converged) return lb_fail(c, LB_ENOTCONVERGED, "GMRES did not converge for a Hodge solve");
+  return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the solve (density gradient): the solve is the linear map
+// u = S S A3^-1 P f with P = I - 1 w^T / |Gamma| the weighted mean
+// projection, so a gradient g_u of u gives g_f = P^T A3^-T S^T S^T g_u, with
+// P^T z = z - w sum(z) / |Gamma|.  Float64 transposed applies and GMRES on A3^T.
+
+// per-block sums of z (fixed order)
+__global__ void k_sum_plain(int64_t N, const double* __restrict__ z, double* __restrict__ partial) {
+  __shared__ double sh[256];
+  double s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    s += z[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void k_proj_t(int64_t N, const double* __restrict__ z, const double* __restrict__ w,
+                         const double* __restrict__ partial, int npart, double area, double* __restrict__ out) {
+  __shared__ double eta;
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < npart; ++k) s += partial[k];
+    eta = s / area;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = z[i] - w[i] * eta;
+}
+
+extern "C" int lb_solve_lb_adjoint(lb_ctx* c, int nrhs, const double* gu, double* gf, lb_solve_info* info) {
+  LB_CHECK(lb_require_corr(c));
+  if (c->params.formulation != LB_A3) return lb_fail(c, LB_EINVAL, "the adjoint solve takes the A3 formulation");
+  if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
+  LB_CUDA(c, cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  if (info) {
+    *info = lb_solve_info{};
+    info->converged = 1;
+    info->nrhs = nrhs;
+  }
+  lb_pair_counter = 0;
+  lb_apply64_counter = lb_apply32_counter = 0;
+  const double* din;
+  double* dout;
+  LB_CHECK(lb_stage_in(c, gu, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
+  LB_CHECK(lb_stage_out(c, gf, nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dout));
+  LB_CHECK(lb_ensure(c, c->ws_quad, (size_t)(3 * N + GM_RB) * sizeof(double)));
+  double* t1 = (double*)c->ws_quad.p;
+  double* t2 = t1 + N;
+  double* z = t2 + N;
+  double* partial = z + N;
+  const unsigned nb = vec_blocks(c);
+  for (int r = 0; r < nrhs; ++r) {
+    LB_CHECK(lb_apply_st_dev(c, din + (int64_t)r * N, t1));
+    LB_CHECK(lb_apply_st_dev(c, t1, t2));
+    int it = 0;
+    double res = 0;
+    std::vector<double> hist;
+    c->adjoint = true;
+    const int rc = gmres(c, LB_FP64, t2, z, c->params.tol, c->params.max_iter, &it, &res, r == 0 ? &hist : nullptr);
+    c->adjoint = false;
+    LB_CHECK(rc);
+    k_sum_plain<<<GM_RB, 256, 0, c->stream>>>(N, z, partial);
+    LB_LAUNCH(c);
+    k_proj_t<<<nb, 256, 0, c->stream>>>(N, z, c->w, partial, GM_RB, c->area, dout + (int64_t)r * N);
+    LB_LAUNCH(c);
+    if (info) {
+      info->iterations += it;
+      info->converged = info->converged && (res < c->params.tol);
+      info->rel_residual = std::max(info->rel_residual, res);
+      if (r == 0) {
+        info->history_len = (int32_t)std::min<size_t>(hist.size(), 128);
+        for (int i = 0; i < info->history_len; ++i) info->history[i] = hist[i];
+      }
+    }
+  }
+  LB_CHECK(lb_stage_out_finish(c, gf, dout, nrhs * N * sizeof(double)));
+  if (info) {
+    info->pairs = lb_pair_counter;
+    info->applies_fp64 = lb_apply64_counter;
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!info->converged) return lb_fail(c, LB_ENOTCONVERGED, "adjoint GMRES did not reach tol %.3g (residual %.3g)",
+                                         c->params.tol, info->rel_residual);
+  }
   return LB_OK;
 }
