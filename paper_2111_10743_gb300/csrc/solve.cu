@@ -311,7 +311,10 @@ static int apply_S_dev(lb_ctx* c, int prec, const double* s, double* out) {
 //   then x_{k+1} = x_k + GMRES32(r_k), r_{k+1} = r_k - A32 delta: delta is
 //   about inner_tol |x|, so float32 pairs (relative 1e-7) keep this update
 //   accurate to about 1e-7 inner_tol |b|;
-//   u = (S^2 x1 or S x1) + S32-potential of (x - x1), for the same reason.
+//   u = (S^2 x1 or S x1) + the float32 potentials of the corrections, for
+//   the same reason; each update apply A32 delta computes the potential of
+//   delta on the way (S^2 delta in A3's second pass, S delta in the first
+//   pass of A2 and A1), and x - x1 is the sum of the deltas.
 static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch, lb_solve_info* info, int first,
                      double* u_out) {
   const int64_t N = c->N;
@@ -333,12 +336,13 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
     double* Ax = scratch + 2 * N;
     double* x1 = scratch + 3 * N;
     double* ux1 = scratch + 4 * N;
-    double* tmp = scratch + 5 * N;
+    double* uacc = scratch + 5 * N;  // float32 solution potential of x - x1
     double nbv = 0, rn = 0;
     LB_CHECK(norm2(c, b, &nbv));
     LB_CUDA(c, cudaMemsetAsync(sigma, 0, N * sizeof(double), c->stream));
     LB_CUDA(c, cudaMemsetAsync(x1, 0, N * sizeof(double), c->stream));
     LB_CUDA(c, cudaMemsetAsync(ux1, 0, N * sizeof(double), c->stream));
+    LB_CUDA(c, cudaMemsetAsync(uacc, 0, N * sizeof(double), c->stream));
     LB_CUDA(c, cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     bool ok = nbv == 0.0;
     int steps = 0;
@@ -362,8 +366,13 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
         k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, Ax, 1.0, r);
         LB_LAUNCH(c);
       } else {
+        // r -= A32 delta; the apply's passes also hold the solution potential
+        // of delta (S[S[delta]] for A3, S[delta] otherwise), accumulated for u
         LB_CHECK(lb_apply_op(c, p.formulation, LB_FP32, delta, Ax));
         k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, Ax, 1.0, r);
+        LB_LAUNCH(c);
+        const double* pot = (const double*)c->ws_pot.p;
+        k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, p.formulation == LB_A3 ? pot + N : pot, 1.0, uacc);
         LB_LAUNCH(c);
       }
       LB_CHECK(norm2(c, r, &rn));
@@ -379,15 +388,9 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
       info->converged = info->converged && ok;
       info->rel_residual = std::max(info->rel_residual, rel);
     }
-    if (u_out) {  // u = u(x1) + float32 potential of x - x1
-      LB_CUDA(c, cudaMemcpyAsync(tmp, sigma, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, x1, 1.0, tmp);
-      LB_LAUNCH(c);
-      LB_CHECK(apply_S_dev(c, LB_FP32, tmp, Ax));
-      if (p.formulation == LB_A3) LB_CHECK(apply_S_dev(c, LB_FP32, Ax, tmp));
-      else LB_CUDA(c, cudaMemcpyAsync(tmp, Ax, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (u_out) {  // u = u(x1) + the float32 potentials of the later corrections (x - x1 = their sum)
       LB_CUDA(c, cudaMemcpyAsync(u_out, ux1, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, tmp, 1.0, u_out);
+      k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, uacc, 1.0, u_out);
       LB_LAUNCH(c);
     }
   }
@@ -411,7 +414,7 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
 // The iteration index j lives on the device and the active systems travel
 // as a kernel argument, so one iteration is a fixed sequence of launches:
 // captured once as a CUDA graph per active set and replayed (parameter
-// `graphs`, unless per-kernel profiling is on), or launched directly; both
+// `graphs`), or launched directly; both
 // run the same kernels on the same data and give identical results.
 //
 // Workspace: V [m+1][R][N] (the j-th vectors of all systems adjacent), the
@@ -873,7 +876,7 @@ static int solve_lockstep(lb_ctx* c, int R, const double* b, double* sigma, doub
   const int64_t RN = (int64_t)R * N;
   Lockstep L;
   LB_CHECK(lockstep_work(c, R, p.max_iter, &L));
-  LB_CHECK(lb_ensure(c, c->ws_bvec, (size_t)(7 * RN) * sizeof(double)));
+  LB_CHECK(lb_ensure(c, c->ws_bvec, (size_t)(8 * RN) * sizeof(double)));
   double* r = (double*)c->ws_bvec.p;  // residuals [R][N]
   double* delta = r + RN;             // corrections (gathered) [Ra][N]
   double* Ax = delta + RN;            // apply output (gathered)
@@ -881,6 +884,7 @@ static int solve_lockstep(lb_ctx* c, int R, const double* b, double* sigma, doub
   double* ux1 = x1 + RN;              // their double-float potentials S[S[x1]]
   double* tmp = ux1 + RN;
   double* rin = tmp + RN;             // gathered residuals
+  double* uacc = rin + RN;            // float32 solution potentials of x - x1
   std::vector<double> hist;
   std::vector<int> its;
   std::vector<double> res;
@@ -902,6 +906,7 @@ static int solve_lockstep(lb_ctx* c, int R, const double* b, double* sigma, doub
     LB_CUDA(c, cudaMemsetAsync(sigma, 0, RN * sizeof(double), c->stream));
     LB_CUDA(c, cudaMemsetAsync(x1, 0, RN * sizeof(double), c->stream));
     LB_CUDA(c, cudaMemsetAsync(ux1, 0, RN * sizeof(double), c->stream));
+    LB_CUDA(c, cudaMemsetAsync(uacc, 0, RN * sizeof(double), c->stream));
     LB_CUDA(c, cudaMemcpyAsync(r, b, RN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     std::vector<int> act;
     std::vector<double> rel(R, 0.0);
@@ -937,9 +942,12 @@ static int solve_lockstep(lb_ctx* c, int R, const double* b, double* sigma, doub
       } else {
         // r -= A32 delta: delta is about inner_tol |x|, so float32 pairs keep
         // this update accurate to about 1e-7 inner_tol |b|
-        LB_CHECK(lb_apply_a3_batch(c, LB_FP32, Ra, delta, Ax, nullptr));
+        // (the apply also yields S[S[delta]], accumulated for u)
+        LB_CHECK(lb_apply_a3_batch(c, LB_FP32, Ra, delta, Ax, tmp));
         for (int a = 0; a < Ra; ++a) {
           k_axpby<<<nb, 256, 0, c->stream>>>(N, -1.0, Ax + (int64_t)a * N, 1.0, r + (int64_t)act[a] * N);
+          LB_LAUNCH(c);
+          k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, tmp + (int64_t)a * N, 1.0, uacc + (int64_t)act[a] * N);
           LB_LAUNCH(c);
         }
       }
@@ -961,14 +969,9 @@ static int solve_lockstep(lb_ctx* c, int R, const double* b, double* sigma, doub
       info->converged = info->converged && (rel[k] < p.tol);
       info->rel_residual = std::max(info->rel_residual, rel[k]);
     }
-    // u = S[S[x1]] (double-float) + float32 potential of x - x1
-    LB_CUDA(c, cudaMemcpyAsync(tmp, sigma, RN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    k_axpby<<<nb, 256, 0, c->stream>>>(RN, -1.0, x1, 1.0, tmp);
-    LB_LAUNCH(c);
-    LB_CHECK(lb_apply_s_batch(c, LB_FP32, R, tmp, Ax));
-    LB_CHECK(lb_apply_s_batch(c, LB_FP32, R, Ax, tmp));
+    // u = S[S[x1]] (double-float) + the float32 potentials of the corrections
     LB_CUDA(c, cudaMemcpyAsync(u, ux1, RN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    k_axpby<<<nb, 256, 0, c->stream>>>(RN, 1.0, tmp, 1.0, u);
+    k_axpby<<<nb, 256, 0, c->stream>>>(RN, 1.0, uacc, 1.0, u);
     LB_LAUNCH(c);
   }
   if (first) {
