@@ -345,3 +345,45 @@ def test_planted_missing_curvature_term_breaks_spectrum(sphere, monkeypatch):
     Af = sphere.apply_A3(f)[0]
     assert np.abs(Af - _golden_spectrum()[3]["A3"] * f).max() > 1e-2
     del L
+
+
+def test_transpose_formulas_against_dense_oracle(cfg1):
+    """The formulas the adjoint path evaluates (transposed far sums over the
+    i with patch(j) not in Near(i), weight w_j outside the sum, the normals'
+    roles swapped in (S''+D')^T, transposed correction blocks) reproduce the
+    transposes of the oracle's dense S and A3 on the unit sphere."""
+    from oracle.gmres import dense_matrix
+    w_, d = cfg1
+    g = d.geo
+    N, npp = g.N, g.np_
+    X, n, w = g.X, g.n, g.w
+    near = np.zeros((N, g.npatch), bool)
+    for i in range(N):
+        near[i, d.near_patch[d.near_ptr[i]:d.near_ptr[i + 1]]] = True
+    far_T = ~near[:, np.arange(N) // npp].T           # [j, i]: patch(j) not in Near(i)
+    C = np.zeros((4, N, N))
+    for i in range(N):
+        for b in range(d.near_ptr[i], d.near_ptr[i + 1]):
+            P = d.near_patch[b]
+            C[:, i, P * npp:(P + 1) * npp] = d.vals[b]
+    dd = X[:, None, :] - X[None, :, :]                # dd[j, i] = x_j - x_i
+    r = np.linalg.norm(dd, axis=2)
+    np.fill_diagonal(r, 1.0)
+    nyd = np.einsum("ik,jik->ji", n, dd)              # n_i . d
+    e = n[None, :, :] - n[:, None, :]                 # n_i - n_j
+    ed = np.einsum("jik,jik->ji", e, dd)
+    e2 = np.einsum("jik,jik->ji", e, e)
+    g4 = 4.0 * np.pi
+    KS = np.where(far_T, 1.0 / (g4 * r), 0.0)
+    KSp = np.where(far_T, nyd / (g4 * r ** 3), 0.0)
+    KSD = np.where(far_T, (3.0 * nyd * ed / r ** 2 - 0.5 * e2) / (g4 * r ** 3), 0.0)
+    St = lambda v: w * (KS @ v) + C[0].T @ v
+    Spt = lambda v: w * (KSp @ v) + C[2].T @ v
+    SDt = lambda v: w * (KSD @ v) + C[3].T @ v
+    y = np.random.default_rng(9).standard_normal(N)
+    Sd = dense_matrix(lambda x: d.S(x), N)
+    Ad = dense_matrix(lambda x: d.apply("A3", x), N)
+    assert np.abs(St(y) - Sd.T @ y).max() < 1e-13 * np.abs(Sd.T @ y).max()
+    v0 = St(St(w))
+    At = -0.25 * y + Spt(Spt(y)) - St(SDt(y) + Spt(2.0 * g.H * y)) + y.sum() / w.sum() * v0
+    assert np.abs(At - Ad.T @ y).max() < 1e-13 * np.abs(Ad.T @ y).max()
