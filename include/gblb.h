@@ -273,17 +273,19 @@ int lb_get_profile(lb_ctx* ctx, lb_profile* out);
  * continuous adjoint of S: the discrete matrix carries the quadrature weights
  * of its columns.  y, out [nrhs][N]: host or device.
  * lb_apply_St: out = S^T y.
- * lb_apply_At: out = A3^T y, A3^T = -I/4 + S'^T S'^T - S^T (S''+D')^T
- *   - S^T S'^T 2H + S^T S^T W^T, W^T y = w sum(y) / |Gamma|; the context's
- *   formulation must be LB_A3 (LB_EINVAL otherwise). */
+ * lb_apply_At: out = A^T y for the context's formulation,
+ *   A3^T = -I/4 + S'^T S'^T - S^T (S''+D')^T - S^T S'^T 2H + S^T S^T W^T,
+ *   A2^T = -I/4 + D^T D^T - (S''+D')^T S^T - S'^T 2H S^T + S^T W^T S^T,
+ *   W^T y = w sum(y) / |Gamma|; LB_EINVAL for LB_A1. */
 int lb_apply_St(lb_ctx* ctx, int nrhs, const double* y, double* out);
 int lb_apply_At(lb_ctx* ctx, int nrhs, const double* y, double* out);
 
-/* Adjoint of lb_solve_lb for the A3 formulation (not in the paper): the solve
- * is the linear map u = S S A3^-1 P f with P = I - 1 w^T / |Gamma| the
- * weighted mean projection, so the gradient of a loss with respect to f is
- * g_f = P^T A3^-T S^T S^T g_u, P^T z = z - w sum(z) / |Gamma|.  GMRES on A3^T
- * (float64 pairs, the context's tol and max_iter).  g_u, g_f [nrhs][N]: host
+/* Adjoint of lb_solve_lb (not in the paper): the solve is a linear map,
+ * u = S S A3^-1 P f (A3) or u = S A2^-1 S P f (A2), P = I - 1 w^T / |Gamma|
+ * the weighted mean projection, so the gradient of a loss with respect to f
+ * is g_f = P^T A3^-T S^T S^T g_u or P^T S^T A2^-T S^T g_u, with
+ * P^T z = z - w sum(z) / |Gamma|.  GMRES on A^T (float64 pairs, the
+ * context's tol and max_iter); LB_EINVAL for LB_A1.  g_u, g_f [nrhs][N]: host
  * or device.  info as for lb_solve_lb (may be NULL); LB_ENOTCONVERGED when
  * GMRES does not reach tol. */
 int lb_solve_lb_adjoint(lb_ctx* ctx, int nrhs, const double* gu, double* gf, lb_solve_info* info);

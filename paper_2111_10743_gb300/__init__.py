@@ -324,12 +324,12 @@ class Context:
         return self._apply(_lib.lb_apply_St, y, out)
 
     def apply_At(self, y, out=None):
-        """A3^T y (the transpose of the discrete A3 operator)."""
+        """A^T y (the transpose of the discrete A3 or A2 operator)."""
         return self._apply(_lib.lb_apply_At, y, out)
 
     def solve_lb_adjoint(self, gu, out=None, allow_unconverged=False):
         """Gradient with respect to f of a loss whose gradient with respect
-        to u = solve_lb(f) is gu (A3 formulation)."""
+        to u = solve_lb(f) is gu (A3 or A2 formulation)."""
         nrhs = self._nrhs(gu)
         p, keep = _ptr(gu, np.float64)
         o, res = _out(out, np.float64, (nrhs, self.N))
@@ -352,7 +352,7 @@ def _torch_fns():
     import torch
 
     class SolveLB(torch.autograd.Function):
-        """u = solve_lb(f) with its density gradient g_f = P^T A3^-T S^T S^T g_u.
+        """u = solve_lb(f) with its density gradient (the adjoint solve).
 
         f: float64 CUDA tensor [nrhs, N]; ctx_lb: a Context with the A3
         formulation and corrections.  The backward pass is the library's
@@ -372,7 +372,7 @@ def _torch_fns():
             return gf, None
 
     class ApplyA(torch.autograd.Function):
-        """y = A3 tau with gradient A3^T g_y."""
+        """y = A tau with gradient A^T g_y."""
 
         @staticmethod
         def forward(ctx, tau, ctx_lb):
@@ -391,10 +391,10 @@ def _torch_fns():
 
 
 def solve_lb_autograd(f, ctx_lb):
-    """Differentiable mean-zero Laplace-Beltrami solve (A3): u = solve(f)."""
+    """Differentiable mean-zero Laplace-Beltrami solve (A3 or A2): u = solve(f)."""
     return _torch_fns()[0].apply(f, ctx_lb)
 
 
 def apply_A_autograd(tau, ctx_lb):
-    """Differentiable A3 apply."""
+    """Differentiable apply of the context's operator (A3 or A2)."""
     return _torch_fns()[1].apply(tau, ctx_lb)

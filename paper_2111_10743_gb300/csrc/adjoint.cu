@@ -20,6 +20,11 @@
 // the transpose of A3 = -I/4 + S'S' - (S''+D')S - 2H S'S + W S S with
 // W = 1 w^T / |Gamma|.  The adjoint of the solve u = S S A3^-1 P f, P the
 // weighted mean projection I - 1 w^T / |Gamma|, is g_f = P^T A3^-T S^T S^T g_u.
+//
+// A2 = -I/4 + D D + S (-(S''+D') - 2H S' + 1 w^T S / |Gamma|) has
+// A2^T y = -y/4 + D^T D^T y - (S''+D')^T t - S'^T (2 H t) + (sum t / |Gamma|) S^T w
+// with t = S^T y, and (D^T y)_j = w_j sum_i -(n_j.d) / (4 pi r^3) y_i + ...;
+// the A2 solve u = S A2^-1 S P f has the adjoint g_f = P^T S^T A2^-T S^T g_u.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,10 +38,11 @@
 #define TT_TS 64  // one 64-bit source mask per tile
 #define TT_TB (TT_NT * TT_NTH)
 
-enum TKind { T_S = 0, T_P1 = 1, T_P2 = 2 };
+enum TKind { T_S = 0, T_P1 = 1, T_P2 = 2, T_DS = 3 };
 template <int K> struct TOut { static const int n = 1; };
 template <> struct TOut<T_P1> { static const int n = 3; };
 template <> struct TOut<T_P2> { static const int n = 2; };
+template <> struct TOut<T_DS> { static const int n = 2; };
 
 // ---------------------------------------------------------------------------
 // transposed near structure
@@ -136,6 +142,12 @@ __device__ __forceinline__ void pair_t(const double* x, const double* nx, const 
   const double rinv = masked ? 0.0 : rsqrt(r2);
   if (KIND == T_S) {
     acc[0] += a.w * rinv;
+    return;
+  }
+  if (KIND == T_DS) {  // D^T q1 (target normal), S^T q1
+    const double nxd = nx[0] * dx + nx[1] * dy + nx[2] * dz;
+    acc[0] -= a.w * nxd * rinv * rinv * rinv;
+    acc[1] += a.w * rinv;
     return;
   }
   const double rinv2 = rinv * rinv, rinv3 = rinv2 * rinv;
@@ -287,7 +299,7 @@ static int pass_t(lb_ctx* c, const double* d1, const double* d2, const CorrT& co
   const int tps = (int)((ntiles + nsplit - 1) / nsplit);
   nsplit = (ntiles + tps - 1) / tps;
   {
-    ProfScope prof(c, LB_PROF_FAR64_K1 + (KIND == T_S ? 0 : 2), N * N);
+    ProfScope prof(c, LB_PROF_FAR64_K1 + (KIND == T_S || KIND == T_DS ? 0 : 2), N * N);
     k_far_t<KIND><<<dim3((unsigned)ntb, (unsigned)nsplit), TT_NTH, 0, c->stream>>>(
         N, c->np, c->pos64, c->nrm64, w.A, w.B, c->tflag, c->tmask, ntiles, tps, w.part);
     LB_LAUNCH(c);
@@ -401,6 +413,69 @@ int lb_apply_a3t(lb_ctx* c, const double* y, double* out) {
   return LB_OK;
 }
 
+// v1 = S^T w, kept until the corrections change
+static int ensure_v1(lb_ctx* c) {
+  if (c->v1) return LB_OK;
+  LB_CHECK(lb_build_transpose(c));
+  LB_CHECK(lb_alloc(c, &c->v1, (size_t)c->N));
+  TWork w;
+  LB_CHECK(work_t(c, &w));
+  return apply_st(c, c->w, c->v1);
+}
+
+__global__ void k_a2t_final(int64_t N, const double* __restrict__ y, const double* __restrict__ b1,
+                            const double* __restrict__ sd, const double* __restrict__ sp2h,
+                            const double* __restrict__ v1, const double* __restrict__ partial, int npart,
+                            double area, double* __restrict__ out) {
+  __shared__ double eta;
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < npart; ++k) s += partial[k];
+    eta = s / area;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = -0.25 * y[i] + b1[i] - sd[i] - sp2h[i] + eta * v1[i];
+}
+
+int lb_apply_a2t(lb_ctx* c, const double* y, double* out) {
+  LB_CHECK(lb_build_transpose(c));
+  LB_CHECK(ensure_v1(c));
+  const int64_t N = c->N;
+  TWork w;
+  LB_CHECK(work_t(c, &w));
+  double* a = vec_t(c, 0);    // [2][N]: D^T y, t = S^T y
+  double* t2 = vec_t(c, 2);   // 2 H t
+  double* o = vec_t(c, 3);    // [3][N]: S'^T t (unused), (S''+D')^T t, S'^T (2 H t)
+  double* b = vec_t(c, 6);    // [2][N]: D^T a0, S^T a0 (unused)
+  double* partial = vec_t(c, 12);
+  CorrT c1{};
+  c1.nout = 2;
+  c1.kern[0] = LB_K_D; c1.dens[0] = y; c1.out[0] = a;
+  c1.kern[1] = LB_K_S; c1.dens[1] = y; c1.out[1] = a + N;
+  LB_CHECK(pass_t<T_DS>(c, y, nullptr, c1, a));
+  k_scale_h<<<lb_div_up(N, 256), 256, 0, c->stream>>>(N, c->H, a + N, t2);
+  LB_LAUNCH(c);
+  CorrT c2{};
+  c2.nout = 3;
+  c2.kern[0] = LB_K_SP; c2.dens[0] = a + N; c2.out[0] = o;
+  c2.kern[1] = LB_K_SPPDP; c2.dens[1] = a + N; c2.out[1] = o + N;
+  c2.kern[2] = LB_K_SP; c2.dens[2] = t2; c2.out[2] = o + 2 * N;
+  LB_CHECK(pass_t<T_P1>(c, a + N, t2, c2, o));
+  CorrT c3{};
+  c3.nout = 2;
+  c3.kern[0] = LB_K_D; c3.dens[0] = a; c3.out[0] = b;
+  c3.kern[1] = LB_K_S; c3.dens[1] = a; c3.out[1] = b + N;
+  LB_CHECK(pass_t<T_DS>(c, a, nullptr, c3, b));
+  k_sum_t<<<T_RB, 256, 0, c->stream>>>(N, a + N, partial);
+  LB_LAUNCH(c);
+  const unsigned nb = (unsigned)std::min<int64_t>(4 * c->sm_count, lb_div_up(N, 256));
+  k_a2t_final<<<nb, 256, 0, c->stream>>>(N, y, b, o + N, o + 2 * N, c->v1, partial, T_RB, c->area, out);
+  LB_LAUNCH(c);
+  ++lb_apply64_counter;
+  return LB_OK;
+}
+
 int lb_apply_st_dev(lb_ctx* c, const double* y, double* out) {
   LB_CHECK(lb_build_transpose(c));
   return apply_st(c, y, out);
@@ -411,8 +486,13 @@ int lb_apply_st_dev(lb_ctx* c, const double* y, double* out) {
 
 static int check_adjoint(lb_ctx* c) {
   LB_CHECK(lb_require_corr(c));
-  if (c->params.formulation != LB_A3) return lb_fail(c, LB_EINVAL, "transposed applies take the A3 formulation");
+  if (c->params.formulation != LB_A3 && c->params.formulation != LB_A2)
+    return lb_fail(c, LB_EINVAL, "transposed applies take the A3 or A2 formulation");
   return LB_OK;
+}
+
+int lb_apply_at_op(lb_ctx* c, const double* y, double* out) {
+  return c->params.formulation == LB_A2 ? lb_apply_a2t(c, y, out) : lb_apply_a3t(c, y, out);
 }
 
 extern "C" int lb_apply_St(lb_ctx* c, int nrhs, const double* y, double* out) {
@@ -437,6 +517,6 @@ extern "C" int lb_apply_At(lb_ctx* c, int nrhs, const double* y, double* out) {
   double* dout;
   LB_CHECK(lb_stage_in(c, y, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
   LB_CHECK(lb_stage_out(c, out, nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dout));
-  for (int r = 0; r < nrhs; ++r) LB_CHECK(lb_apply_a3t(c, din + (int64_t)r * N, dout + (int64_t)r * N));
+  for (int r = 0; r < nrhs; ++r) LB_CHECK(lb_apply_at_op(c, din + (int64_t)r * N, dout + (int64_t)r * N));
   return lb_stage_out_finish(c, out, dout, nrhs * N * sizeof(double));
 }

@@ -240,6 +240,7 @@ static void free_geometry(lb_ctx* c) {
 void lb_free_transpose(lb_ctx* c) {
   lb_free(&c->tptr); lb_free(&c->trow); lb_free(&c->tblk); lb_free(&c->tmask); lb_free(&c->tflag);
   lb_free(&c->v0);
+  lb_free(&c->v1);
   c->have_trans = false;
 }
 

@@ -102,6 +102,7 @@ struct lb_ctx {
   uint8_t* tflag = nullptr;               // [target blocks][tiles]
   int64_t t_ntiles = 0, t_ntb = 0;
   double* v0 = nullptr;                   // S^T S^T w
+  double* v1 = nullptr;                   // S^T w
   bool adjoint = false;                   // GMRES applies A3^T
   std::map<const void*, int> occupancy;  // resident blocks per SM, per kernel (queried once)
 
@@ -201,6 +202,8 @@ int lb_apply_a1(lb_ctx* c, int prec, const double* tau, double* out);
 // transposes (float64): A3^T y, S^T y (device in, device out)
 int lb_apply_a3t(lb_ctx* c, const double* y, double* out);
 int lb_apply_st_dev(lb_ctx* c, const double* y, double* out);
+// A3^T or A2^T by the context's formulation
+int lb_apply_at_op(lb_ctx* c, const double* y, double* out);
 int lb_build_transpose(lb_ctx* c);
 void lb_free_transpose(lb_ctx* c);
 int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out);

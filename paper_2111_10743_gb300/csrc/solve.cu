@@ -253,7 +253,7 @@ static int gmres(lb_ctx* c, int prec, const double* b, double* x, double tol, in
   double r = 1.0;
   for (int j = 0; j < max_iter; ++j) {
     const double* vj = G.V + (int64_t)j * N;
-    if (c->adjoint) LB_CHECK(lb_apply_a3t(c, vj, G.w));
+    if (c->adjoint) LB_CHECK(lb_apply_at_op(c, vj, G.w));
     else LB_CHECK(lb_apply_op(c, c->params.formulation, prec, vj, G.w));
     LB_CHECK(arnoldi_step(c, G, j, beta));
     LB_CHECK(read_scalar(c, G.scal, &r));
@@ -1376,7 +1376,9 @@ __global__ void k_proj_t(int64_t N, const double* __restrict__ z, const double* 
 
 extern "C" int lb_solve_lb_adjoint(lb_ctx* c, int nrhs, const double* gu, double* gf, lb_solve_info* info) {
   LB_CHECK(lb_require_corr(c));
-  if (c->params.formulation != LB_A3) return lb_fail(c, LB_EINVAL, "the adjoint solve takes the A3 formulation");
+  const bool a2 = c->params.formulation == LB_A2;
+  if (c->params.formulation != LB_A3 && !a2)
+    return lb_fail(c, LB_EINVAL, "the adjoint solve takes the A3 or A2 formulation");
   if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
   LB_CUDA(c, cudaSetDevice(c->device));
   const int64_t N = c->N;
@@ -1398,8 +1400,11 @@ extern "C" int lb_solve_lb_adjoint(lb_ctx* c, int nrhs, const double* gu, double
   double* partial = z + N;
   const unsigned nb = vec_blocks(c);
   for (int r = 0; r < nrhs; ++r) {
+    // A3: solve A3^T z = S^T S^T g_u, g_f = P^T z;
+    // A2: solve A2^T z = S^T g_u,     g_f = P^T S^T z
     LB_CHECK(lb_apply_st_dev(c, din + (int64_t)r * N, t1));
-    LB_CHECK(lb_apply_st_dev(c, t1, t2));
+    if (a2) LB_CUDA(c, cudaMemcpyAsync(t2, t1, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    else LB_CHECK(lb_apply_st_dev(c, t1, t2));
     int it = 0;
     double res = 0;
     std::vector<double> hist;
@@ -1407,6 +1412,10 @@ extern "C" int lb_solve_lb_adjoint(lb_ctx* c, int nrhs, const double* gu, double
     const int rc = gmres(c, LB_FP64, t2, z, c->params.tol, c->params.max_iter, &it, &res, r == 0 ? &hist : nullptr);
     c->adjoint = false;
     LB_CHECK(rc);
+    if (a2) {
+      LB_CHECK(lb_apply_st_dev(c, z, t1));
+      LB_CUDA(c, cudaMemcpyAsync(z, t1, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    }
     k_sum_plain<<<GM_RB, 256, 0, c->stream>>>(N, z, partial);
     LB_LAUNCH(c);
     k_proj_t<<<nb, 256, 0, c->stream>>>(N, z, c->w, partial, GM_RB, c->area, dout + (int64_t)r * N);

@@ -24,29 +24,32 @@ def lb():
     return lb
 
 
-def dense(name):
-    """Dense S and A3 of the oracle's discretisation."""
-    if name not in _DENSE:
+def dense(name, form="A3"):
+    """Dense S and A3 (or A2) of the oracle's discretisation."""
+    if (name, form) not in _DENSE:
         from oracle.gmres import dense_matrix
         s, d = oracle_disc(name)
         N = d.geo.N
-        _DENSE[name] = (dense_matrix(lambda x: d.S(x), N), dense_matrix(lambda x: d.apply("A3", x), N))
-    return _DENSE[name]
+        _DENSE[(name, form)] = (dense_matrix(lambda x: d.S(x), N), dense_matrix(lambda x: d.apply(form, x), N))
+    return _DENSE[(name, form)]
 
 
 @pytest.mark.parametrize("name", ["sphere300", "ellipsoid1200"])
-def test_transposed_operators(lb, name):
-    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3, precision=lb.LB_FP64)
-    Smat, Amat = dense(name)
+@pytest.mark.parametrize("form", ["A3", "A2"])
+def test_transposed_operators(lb, name, form):
+    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3 if form == "A3" else lb.LB_A2, precision=lb.LB_FP64)
+    Smat, Amat = dense(name, form)
     y = np.random.default_rng(40).standard_normal((2, d.geo.N))
     assert _rel(ctx.apply_St(y), y @ Smat) < 1e-12
     assert _rel(ctx.apply_At(y), y @ Amat) < 1e-12
 
 
 @pytest.mark.parametrize("name", ["sphere300", "ellipsoid1200"])
-def test_adjoint_solve_matches_dense_gradient(lb, name):
-    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3, precision=lb.LB_FP64, tol=1e-14)
-    Smat, Amat = dense(name)
+@pytest.mark.parametrize("form", ["A3", "A2"])
+def test_adjoint_solve_matches_dense_gradient(lb, name, form):
+    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3 if form == "A3" else lb.LB_A2, precision=lb.LB_FP64,
+                        tol=1e-14)
+    Smat, Amat = dense(name, form)
     g = d.geo
     N = g.N
     rng = np.random.default_rng(41)
@@ -58,9 +61,9 @@ def test_adjoint_solve_matches_dense_gradient(lb, name):
     # adjoint identity of the linear map f -> u
     lhs, rhs = float(np.sum(gu * u)), float(np.sum(gf * f))
     assert abs(lhs - rhs) < 1e-10 * np.linalg.norm(gu) * np.linalg.norm(u) * 10
-    # dense gradient: u = S S A3^-1 P f, P = I - 1 w^T / |Gamma|
+    # dense gradient: u = S S A3^-1 P f or S A2^-1 S P f, P = I - 1 w^T / |Gamma|
     P = np.eye(N) - np.outer(np.ones(N), g.w) / g.w.sum()
-    L = Smat @ Smat @ np.linalg.solve(Amat, P)
+    L = Smat @ Smat @ np.linalg.solve(Amat, P) if form == "A3" else Smat @ np.linalg.solve(Amat, Smat @ P)
     assert _rel2(gf[0], L.T @ gu[0]) < 1e-9
     assert _rel2(u[0], L @ f[0]) < 1e-9
 
@@ -96,8 +99,8 @@ def test_autograd_solve_and_apply(lb):
     assert _rel(tau.grad.cpu().numpy(), gy.cpu().numpy() @ Amat) < 1e-12
 
 
-def test_adjoint_requires_A3(lb):
-    ctx, s, d = ctx_for(lb, "sphere300", formulation=lb.LB_A2, precision=lb.LB_FP64)
+def test_adjoint_refuses_A1(lb):
+    ctx, s, d = ctx_for(lb, "sphere300", formulation=lb.LB_A1, precision=lb.LB_FP64)
     with pytest.raises(lb.LBError) as e:
         ctx.apply_At(np.zeros((1, d.geo.N)))
     assert e.value.code == lb.LB_EINVAL
