@@ -347,6 +347,30 @@ def test_planted_missing_curvature_term_breaks_spectrum(sphere, monkeypatch):
     del L
 
 
+def test_harmonic_fields_torus_closed_form():
+    """Harmonic fields (Section 5) on a torus: the azimuthal angle theta of a
+    surface of revolution is harmonic, so grad_Gamma theta = e_theta / rho
+    and n x grad_Gamma theta are the torus's two harmonic fields.  Their
+    decomposition returns them unchanged; added gradient and rotated-gradient
+    parts are removed, up to this coarse (order-4, 64-patch) discretisation.
+    A wrong sign in either potential equation would leave an O(1) error."""
+    from oracle.geometry import surface_gradient
+    from oracle.hodge import harmonic_field
+    s = S.torus(2.0, 0.75, 8, 4, 4)
+    d = discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0, eps_q=1e-10, workers=WORKERS)
+    g = d.geo
+    x, y, z = g.X.T
+    gth = np.stack([-y, x, 0.0 * x], 1) / (x * x + y * y)[:, None]
+    wl2 = lambda F: np.sqrt(np.sum(g.w * np.sum(F * F, 1)))
+    for F in (gth, np.cross(g.n, gth)):
+        H, nH, _ = harmonic_field(d, F)
+        assert wl2(H - F) < 5e-4 * wl2(F)
+        assert np.abs(nH - np.cross(g.n, H)).max() == 0.0
+    G = surface_gradient(g, np.sin(x) * np.cos(0.7 * y) + z * z)
+    H, _, _ = harmonic_field(d, gth + G + np.cross(g.n, G))
+    assert wl2(H - gth) < 0.4 * wl2(gth)
+
+
 def test_transpose_formulas_against_dense_oracle(cfg1):
     """The formulas the adjoint path evaluates (transposed far sums over the
     i with patch(j) not in Near(i), weight w_j outside the sum, the normals'
