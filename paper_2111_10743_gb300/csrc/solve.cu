@@ -1,5 +1,6 @@
-// GMRES, the mean-zero Laplace-Beltrami solve, mixed-precision refinement,
-// surface differential operators and harmonic vector fields.
+// GMRES, the mean-zero Laplace-Beltrami solve (single and lockstep), mixed-
+// precision refinement, surface differential operators, harmonic vector
+// fields, the A1 apply and the adjoint solve.
 //
 // GMRES (Section 6: relative residual below tol, at most max_iter = 100
 // iterations): x0 = 0, no restart, Euclidean inner product.  The Arnoldi
@@ -13,8 +14,13 @@
 // Mixed precision (LB_FP32_REFINED): float32 pair sums are accurate to about
 // 1e-6, so an inner GMRES on the float32 operator to inner_tol is wrapped in
 // iterative refinement whose residual b - A x uses double-float pair sums
-// (about 1e-14, several times faster than float64 on GB300); the solution
-// potentials u = S[S[sigma]] use them too.
+// (about 1e-14, several times faster than float64 on GB300).  The solution
+// potential is that apply's S[S[x1]] plus the float32 potentials that the
+// later update applies compute on the way.
+//
+// Several right-hand sides (A3) advance in lockstep with one batched apply
+// per iteration, each iteration replayed as a captured CUDA graph; see the
+// Lockstep section below.
 //
 // Surface operators (Section 2), by nodal differentiation within a patch:
 //   grad_Gamma f = (g^11 f_u + g^12 f_v) X_u + (g^21 f_u + g^22 f_v) X_v,
