@@ -14,6 +14,7 @@ Modules (paper section in brackets):
   layers     discretised potentials, the A2 and A3 operators               [3, 4.2, 4.3]
   gmres      GMRES, dense assembly and the mean-zero solve                 [6]
   hodge      surface div / grad and the harmonic-field decomposition       [2, 5]
+  shape      gradient of an A3-solve loss with respect to node positions
 
 Parity status: every function here is pinned by a closed form, an invariant
 or a library special case in tests/test_oracle_*.py, except the corrected

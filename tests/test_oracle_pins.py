@@ -411,3 +411,30 @@ def test_transpose_formulas_against_dense_oracle(cfg1):
     v0 = St(St(w))
     At = -0.25 * y + Spt(Spt(y)) - St(SDt(y) + Spt(2.0 * g.H * y)) + y.sum() / w.sum() * v0
     assert np.abs(At - Ad.T @ y).max() < 1e-13 * np.abs(Ad.T @ y).max()
+
+
+def test_shape_gradient_matches_finite_differences(cfg1):
+    """Gradient of L = |u - u_t|^2 / 2 (u the A3 solve) with respect to the node
+    positions, with corrections, weights, normals and curvature held fixed,
+    against central differences (h = 1e-5, float64) along a random direction."""
+    import dataclasses
+    from oracle.gmres import solve_lb
+    from oracle.shape import shape_gradient_A3
+    w_, d = cfg1
+    g = d.geo
+    rng = np.random.default_rng(3)
+    f = w_.f[0] + 0.3 * rng.standard_normal(g.N)
+    ut = rng.standard_normal(g.N)
+
+    def loss(dd):
+        u, *_ = solve_lb(dd, f, "A3", tol=1e-14)
+        return 0.5 * np.sum((u - ut) ** 2), u
+
+    _, u0 = loss(d)
+    grad = shape_gradient_A3(d, f, u0 - ut)
+    dX = rng.standard_normal((g.N, 3))
+    h = 1e-5
+    Lp = loss(dataclasses.replace(d, geo=dataclasses.replace(g, X=g.X + h * dX)))[0]
+    Lm = loss(dataclasses.replace(d, geo=dataclasses.replace(g, X=g.X - h * dX)))[0]
+    an = np.sum(grad * dX)
+    assert abs((Lp - Lm) / (2 * h) - an) < 1e-7 * abs(an)
