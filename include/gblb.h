@@ -251,6 +251,7 @@ int lb_harmonic_fields(lb_ctx* ctx, int nF, const double* F, double* H, lb_solve
 #define LB_PROF_FARDF_KALL 11
 #define LB_PROF_FARDF_K2 12
 #define LB_PROF_FARDF_K4 13
+#define LB_PROF_SHAPE 14       /* node-position gradient pair sums (float64) */
 #define LB_PROF_NCAT 16
 
 typedef struct {
@@ -289,6 +290,21 @@ int lb_apply_At(lb_ctx* ctx, int nrhs, const double* y, double* out);
  * or device.  info as for lb_solve_lb (may be NULL); LB_ENOTCONVERGED when
  * GMRES does not reach tol. */
 int lb_solve_lb_adjoint(lb_ctx* ctx, int nrhs, const double* gu, double* gf, lb_solve_info* info);
+
+/* Gradient of a loss of the A3 solve with respect to the node positions (not
+ * in the paper).  The positions enter the discrete A3 operator of Sections 3
+ * and 4 only through the far pair sums; the correction weights, the near
+ * lists, w, n and H are held fixed.  With A3 sigma = P f, u = S S sigma,
+ * z = A3^-T S^T S^T g_u and d = x_i - x_j,
+ *   dL = g_u.dS(S sigma) + (S^T g_u).dS(sigma) - z.(dA3 sigma),
+ * each term a sum over far pairs of a_i w_j b_j grad_d K(x_i, x_j).(dx_i - dx_j)
+ * for K = S, S', S''+D'.  Two GMRES solves (A3 and A3^T, float64 pairs, the
+ * context's tol and max_iter) and two float64 gradient pair sums.  f, g_u
+ * [nrhs][N], grad [nrhs][N][3]: host or device.  LB_EINVAL unless the
+ * formulation is LB_A3; info as for lb_solve_lb (iterations of both solves;
+ * may be NULL); LB_ENOTCONVERGED when a GMRES does not reach tol. */
+int lb_shape_gradient(lb_ctx* ctx, int nrhs, const double* f, const double* gu, double* grad,
+                      lb_solve_info* info);
 
 /* Launch shapes chosen by the batched passes' tuner (not part of the paper;
  * several-density passes time each shape once per process and surface and

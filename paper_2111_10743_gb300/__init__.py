@@ -61,7 +61,7 @@ class lb_geom_info(ctypes.Structure):
 PROF_NCAT = 16
 PROF_NAMES = {0: "far32_k1", 1: "far32_kall", 2: "far32_k2", 3: "far32_k4", 4: "far64_k1", 5: "far64_kall",
               6: "far64_k2", 7: "far64_k4", 8: "epilogue_spmv", 9: "quad", 10: "fardf_k1", 11: "fardf_kall",
-              12: "fardf_k2", 13: "fardf_k4"}
+              12: "fardf_k2", 13: "fardf_k4", 14: "shape_grad"}
 
 
 class lb_profile(ctypes.Structure):
@@ -97,6 +97,7 @@ def _load():
         "lb_set_profiling": [P, ctypes.c_int], "lb_get_profile": [P, P], "lb_get_tuning": [P, P],
         "lb_apply_St": [P, ctypes.c_int, P, P], "lb_apply_At": [P, ctypes.c_int, P, P],
         "lb_solve_lb_adjoint": [P, ctypes.c_int, P, P, P],
+        "lb_shape_gradient": [P, ctypes.c_int, P, P, P, P],
         "lb_far_sums_noalloc": [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P, P],
     }
     for name, args in sig.items():
@@ -335,6 +336,21 @@ class Context:
         o, res = _out(out, np.float64, (nrhs, self.N))
         info = lb_solve_info()
         self._check(_lib.lb_solve_lb_adjoint(self._h, nrhs, p, o, ctypes.byref(info)),
+                    allow=(LB_ENOTCONVERGED,) if allow_unconverged else ())
+        return res, info.as_dict()
+
+    def shape_gradient(self, f, gu, out=None, allow_unconverged=False):
+        """Gradient [nrhs, N, 3] with respect to the node positions of a loss
+        whose gradient with respect to u = solve_lb(f) is gu (A3, corrections
+        held fixed)."""
+        nrhs = self._nrhs(f)
+        if self._nrhs(gu) != nrhs:
+            raise ValueError("f and gu need the same number of right-hand sides")
+        p, keep = _ptr(f, np.float64)
+        q, keep2 = _ptr(gu, np.float64)
+        o, res = _out(out, np.float64, (nrhs, self.N, 3))
+        info = lb_solve_info()
+        self._check(_lib.lb_shape_gradient(self._h, nrhs, p, q, o, ctypes.byref(info)),
                     allow=(LB_ENOTCONVERGED,) if allow_unconverged else ())
         return res, info.as_dict()
 

@@ -520,3 +520,314 @@ extern "C" int lb_apply_At(lb_ctx* c, int nrhs, const double* y, double* out) {
   for (int r = 0; r < nrhs; ++r) LB_CHECK(lb_apply_at_op(c, din + (int64_t)r * N, dout + (int64_t)r * N));
   return lb_stage_out_finish(c, out, dout, nrhs * N * sizeof(double));
 }
+
+// ---------------------------------------------------------------------------
+// Node-position gradient of a loss of the A3 solve (float64).
+//
+// The positions enter A3 only through the far pair sums; the corrections, the
+// near lists, w, n and H are held fixed.  With A3 sigma = P f, u = S S sigma,
+// mu1 = S' sigma, mu2 = S sigma, q1 = S^T g_u and z = A3^-T S^T S^T g_u,
+//   dL = g_u.dS(mu2) + q1.dS(sigma) - z.(dA3 sigma),
+// and every term is a.dK(b) = sum over far pairs of a_i w_j b_j
+// grad_d K(x_i, x_j).(dx_i - dx_j), d = x_i - x_j, normals fixed.  Grouped by
+// (K, b) the six terms are
+//   (S, sigma):  a0 = q1 + (S''+D')^T z + S'^T (2 H z) - eta S^T w,
+//   (S, mu2):    a1 = g_u - eta w,
+//   (S', mu1):   a2 = -z,
+//   (S', sigma): a3 = -S'^T z,
+//   (S', mu2):   a4 = 2 H z,
+//   (S''+D', mu2): a5 = z,
+// eta = sum z / |Gamma|, and grad_i = sum_m a_m,i T_m,i - b_m,i U_m,i with the
+// forward sums T_m,i = sum_j w_j b_m,j grad K_m(x_i, x_j) and the transposed
+// sums U_m,j = w_j sum_i a_m,i grad K_m(x_i, x_j).  The kernels' gradients in
+// d, with a = n_i.d, e = n_i - n_j, b = e.d and 1/(4 pi) applied at the end:
+//   grad S      = -d / r^3,
+//   grad S'     = -n_i / r^3 + 3 a d / r^5,
+//   grad S''+D' = [3 (b n_i + a e) / r^2 - 6 a b d / r^4] / r^3
+//                 - 3 (3 a b / r^2 - |e|^2 / 2) d / r^5.
+#define GR_NTH 128
+#define GR_NO 18  // six (kernel, density) sums x three components
+
+__device__ __forceinline__ void grad_kernels(const double* d, const double* ni, const double* nj, double rinv,
+                                             double* gS, double* gSp, double* gSD) {
+  const double rinv2 = rinv * rinv, rinv3 = rinv2 * rinv, rinv5 = rinv3 * rinv2;
+  const double a = ni[0] * d[0] + ni[1] * d[1] + ni[2] * d[2];
+  const double e[3] = {ni[0] - nj[0], ni[1] - nj[1], ni[2] - nj[2]};
+  const double b = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
+  const double e2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+  const double c1 = 3.0 * rinv5;
+  const double c2 = 6.0 * a * b * rinv2 * rinv5 + 3.0 * (3.0 * a * b * rinv2 - 0.5 * e2) * rinv5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gS[k] = -d[k] * rinv3;
+    gSp[k] = -ni[k] * rinv3 + 3.0 * a * d[k] * rinv5;
+    gSD[k] = c1 * (b * ni[k] + a * e[k]) - c2 * d[k];
+  }
+}
+
+// forward sums: targets i, sources j with patch(j) not in Near(i).
+// Q [Npad][3] = w (sigma, mu1, mu2); part [split][18][N]
+__global__ void __launch_bounds__(GR_NTH) k_grad_fwd(int64_t N, int np, const double4_32a* __restrict__ pos,
+                                                     const double4_32a* __restrict__ nrm, const double* __restrict__ Q,
+                                                     const uint8_t* __restrict__ flags, int64_t ntiles,
+                                                     const int64_t* __restrict__ row_ptr,
+                                                     const int32_t* __restrict__ near_patch, int tiles_per_split,
+                                                     double* __restrict__ part) {
+  __shared__ double4_32a sP[TT_TS], sN[TT_TS];
+  __shared__ double sQ[TT_TS][3];
+  __shared__ int sLp[TT_TS];
+  const int64_t t = (int64_t)blockIdx.x * GR_NTH + threadIdx.x;  // < Npad
+  const double4_32a p = pos[t], n = nrm[t];
+  const double xi[3] = {p.x, p.y, p.z}, ni[3] = {n.x, n.y, n.z};
+  double acc[GR_NO];
+#pragma unroll
+  for (int o = 0; o < GR_NO; ++o) acc[o] = 0.0;
+  const int64_t tile_b = (int64_t)blockIdx.y * tiles_per_split;
+  const int64_t tile_e = min(ntiles, tile_b + tiles_per_split);
+  for (int64_t tile = tile_b; tile < tile_e; ++tile) {
+    const int64_t s0 = tile * TT_TS;
+    const int64_t P0 = s0 / np;
+    for (int s = threadIdx.x; s < TT_TS; s += GR_NTH) {
+      sP[s] = pos[s0 + s];
+      sN[s] = nrm[s0 + s];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sQ[s][k] = Q[(s0 + s) * 3 + k];
+      sLp[s] = (int)((s0 + s) / np - P0);  // < 64: a tile spans at most 64 patches
+    }
+    __syncthreads();
+    // bit L: patch P0 + L is in Near(t)
+    unsigned long long m = 0ull;
+    if (flags[(int64_t)blockIdx.x * ntiles + tile] != 0 && t < N)
+      for (int64_t bb = row_ptr[t]; bb < row_ptr[t + 1]; ++bb) {
+        const int64_t dd = (int64_t)near_patch[bb] - P0;
+        if (dd >= 0 && dd < 64) m |= 1ull << dd;
+      }
+    for (int s = 0; s < TT_TS; ++s) {
+      const double4_32a a = sP[s], b = sN[s];
+      const double d[3] = {xi[0] - a.x, xi[1] - a.y, xi[2] - a.z};
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      const bool masked = ((m >> sLp[s]) & 1ull) || t >= N;
+      const double rinv = masked ? 0.0 : rsqrt(r2);
+      const double nj[3] = {b.x, b.y, b.z};
+      double gS[3], gSp[3], gSD[3];
+      grad_kernels(d, ni, nj, rinv, gS, gSp, gSD);
+      const double qs = sQ[s][0], q1 = sQ[s][1], q2 = sQ[s][2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        acc[k] += qs * gS[k];
+        acc[3 + k] += q2 * gS[k];
+        acc[6 + k] += q1 * gSp[k];
+        acc[9 + k] += qs * gSp[k];
+        acc[12 + k] += q2 * gSp[k];
+        acc[15 + k] += q2 * gSD[k];
+      }
+    }
+    __syncthreads();
+  }
+  if (t >= N) return;
+#pragma unroll
+  for (int o = 0; o < GR_NO; ++o) part[((int64_t)blockIdx.y * GR_NO + o) * N + t] = acc[o];
+}
+
+// transposed sums: outputs j, sources i with patch(j) not in Near(i).
+// A [Npad][6] = (a0 .. a5) at the sources; part [split][18][N]
+__global__ void __launch_bounds__(GR_NTH) k_grad_tr(int64_t N, int np, const double4_32a* __restrict__ pos,
+                                                    const double4_32a* __restrict__ nrm, const double* __restrict__ A,
+                                                    const uint8_t* __restrict__ tflag,
+                                                    const unsigned long long* __restrict__ tmask, int64_t ntiles,
+                                                    int tiles_per_split, double* __restrict__ part) {
+  __shared__ double4_32a sP[TT_TS], sN[TT_TS];
+  __shared__ double sA[TT_TS][6];
+  const int64_t t = (int64_t)blockIdx.x * GR_NTH + threadIdx.x;  // < Npad
+  const double4_32a p = pos[t], n = nrm[t];
+  const double xj[3] = {p.x, p.y, p.z}, nj[3] = {n.x, n.y, n.z};
+  const int64_t pj = t < N ? t / np : -1;
+  double acc[GR_NO];
+#pragma unroll
+  for (int o = 0; o < GR_NO; ++o) acc[o] = 0.0;
+  const int64_t tile_b = (int64_t)blockIdx.y * tiles_per_split;
+  const int64_t tile_e = min(ntiles, tile_b + tiles_per_split);
+  for (int64_t tile = tile_b; tile < tile_e; ++tile) {
+    const int64_t s0 = tile * TT_TS;
+    for (int s = threadIdx.x; s < TT_TS; s += GR_NTH) {
+      sP[s] = pos[s0 + s];
+      sN[s] = nrm[s0 + s];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sA[s][k] = A[(s0 + s) * 6 + k];
+    }
+    __syncthreads();
+    // the flag table is per block of TT_TB outputs, which holds this block's GR_NTH
+    const bool any = tflag[((int64_t)blockIdx.x * GR_NTH / TT_TB) * ntiles + tile] != 0;
+    const unsigned long long m = (any && pj >= 0) ? tmask[pj * ntiles + tile] : 0ull;
+    for (int s = 0; s < TT_TS; ++s) {
+      const double4_32a a = sP[s], b = sN[s];
+      const double d[3] = {a.x - xj[0], a.y - xj[1], a.z - xj[2]};  // x_i - x_j
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      const bool masked = ((m >> s) & 1ull) || pj < 0;
+      const double rinv = masked ? 0.0 : rsqrt(r2);
+      const double ni[3] = {b.x, b.y, b.z};
+      double gS[3], gSp[3], gSD[3];
+      grad_kernels(d, ni, nj, rinv, gS, gSp, gSD);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        acc[k] += sA[s][0] * gS[k];
+        acc[3 + k] += sA[s][1] * gS[k];
+        acc[6 + k] += sA[s][2] * gSp[k];
+        acc[9 + k] += sA[s][3] * gSp[k];
+        acc[12 + k] += sA[s][4] * gSp[k];
+        acc[15 + k] += sA[s][5] * gSD[k];
+      }
+    }
+    __syncthreads();
+  }
+  if (t >= N) return;
+#pragma unroll
+  for (int o = 0; o < GR_NO; ++o) part[((int64_t)blockIdx.y * GR_NO + o) * N + t] = acc[o];
+}
+
+// out[o][j] = scale_j / (4 pi) sum_s part[s][o][j], scale = w_j or 1
+__global__ void k_reduce_g(int64_t N, int nsplit, const double* __restrict__ part, const double* __restrict__ w,
+                           double* __restrict__ out) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const double sc = (w ? w[j] : 1.0) * LB_INV4PI;
+  for (int o = 0; o < GR_NO; ++o) {
+    double s = 0;
+    for (int k = 0; k < nsplit; ++k) s += part[((int64_t)k * GR_NO + o) * N + j];
+    out[(int64_t)o * N + j] = s * sc;
+  }
+}
+
+struct GradVecs {
+  const double* v[6];
+};
+
+// out[i][k] = scale_i v_k[i] for i < N, 0 in the padding
+__global__ void k_pack_g(int64_t N, int64_t Npad, int nv, const double* __restrict__ scale, GradVecs gv,
+                         double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= Npad) return;
+  for (int k = 0; k < nv; ++k) out[i * nv + k] = i < N ? (scale ? scale[i] : 1.0) * gv.v[k][i] : 0.0;
+}
+
+// a vectors of the six terms; eta = sum z / area from per-block partials
+__global__ void k_grad_avec(int64_t N, const double* __restrict__ gu, const double* __restrict__ q1,
+                            const double* __restrict__ z, const double* __restrict__ h2z,
+                            const double* __restrict__ tp, const double* __restrict__ v1,
+                            const double* __restrict__ w, const double* __restrict__ partial, int npart, double area,
+                            double* __restrict__ a) {
+  __shared__ double eta;
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int k = 0; k < npart; ++k) s += partial[k];
+    eta = s / area;
+  }
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    a[i] = q1[i] + tp[N + i] + tp[2 * N + i] - eta * v1[i];
+    a[N + i] = gu[i] - eta * w[i];
+    a[2 * N + i] = -z[i];
+    a[3 * N + i] = -tp[i];
+  }
+}
+
+struct GradB {
+  const double* a[6];
+  const double* b[6];
+};
+
+// grad[i][k] = sum_m a_m[i] T[m][k][i] - b_m[i] U[m][k][i]
+__global__ void k_grad_combine(int64_t N, GradB ab, const double* __restrict__ T, const double* __restrict__ U,
+                               double* __restrict__ grad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double g[3] = {0, 0, 0};
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const double am = ab.a[m][i], bm = ab.b[m][i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] += am * T[(int64_t)(3 * m + k) * N + i] - bm * U[(int64_t)(3 * m + k) * N + i];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) grad[i * 3 + k] = g[k];
+}
+
+int lb_shape_grad_pairs(lb_ctx* c, const double* gu, const double* sg, const double* mu1, const double* mu2,
+                        const double* q1, const double* z, double* grad) {
+  LB_CHECK(lb_build_transpose(c));
+  LB_CHECK(ensure_v1(c));
+  const int64_t N = c->N, Npad = c->Npad;
+  MaskTable* mt = nullptr;
+  LB_CHECK(lb_get_mask(c, GR_NTH, TT_TS, &mt));
+  const uint8_t* fflags = mt->flags;
+  const int64_t ntb = (N + GR_NTH - 1) / GR_NTH, ntiles = Npad / TT_TS;
+  if (mt->ntb != ntb || mt->ntiles != ntiles || c->t_ntiles != ntiles)
+    return lb_fail(c, LB_EINVAL, "gradient tile tables disagree");
+  const int64_t want = 6LL * c->sm_count;
+  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>({ntiles, (want + ntb - 1) / ntb, (int64_t)32}));
+  const int tps = (int)((ntiles + nsplit - 1) / nsplit);
+  nsplit = (ntiles + tps - 1) / tps;
+  // vectors: h2z, tp [3], a0..a3 [4], T [18], U [18], partial; scratch: packed [Npad][6], part
+  const size_t nvec = (size_t)(1 + 3 + 4 + 2 * GR_NO) * N + T_RB;
+  LB_CHECK(lb_ensure(c, c->ws_grad, (nvec + (size_t)Npad * 6 + (size_t)nsplit * GR_NO * N) * sizeof(double)));
+  double* h2z = (double*)c->ws_grad.p;
+  double* tp = h2z + N;
+  double* av = tp + 3 * N;
+  double* T = av + 4 * N;
+  double* U = T + GR_NO * N;
+  double* partial = U + GR_NO * N;
+  double* packed = partial + T_RB;
+  double* part = packed + Npad * 6;
+  const unsigned nb = (unsigned)std::min<int64_t>(4 * c->sm_count, lb_div_up(N, 256));
+  k_scale_h<<<lb_div_up(N, 256), 256, 0, c->stream>>>(N, c->H, z, h2z);
+  LB_LAUNCH(c);
+  // S'^T z, (S''+D')^T z, S'^T (2 H z)
+  CorrT c1{};
+  c1.nout = 3;
+  c1.kern[0] = LB_K_SP; c1.dens[0] = z; c1.out[0] = tp;
+  c1.kern[1] = LB_K_SPPDP; c1.dens[1] = z; c1.out[1] = tp + N;
+  c1.kern[2] = LB_K_SP; c1.dens[2] = h2z; c1.out[2] = tp + 2 * N;
+  LB_CHECK(pass_t<T_P1>(c, z, h2z, c1, tp));
+  k_sum_t<<<T_RB, 256, 0, c->stream>>>(N, z, partial);
+  LB_LAUNCH(c);
+  k_grad_avec<<<nb, 256, 0, c->stream>>>(N, gu, q1, z, h2z, tp, c->v1, c->w, partial, T_RB, c->area, av);
+  LB_LAUNCH(c);
+  GradB ab{};
+  const double* avs[6] = {av, av + N, av + 2 * N, av + 3 * N, h2z, z};
+  const double* bvs[6] = {sg, mu2, mu1, sg, mu2, mu2};
+  for (int m = 0; m < 6; ++m) {
+    ab.a[m] = avs[m];
+    ab.b[m] = bvs[m];
+  }
+  // forward sums of w (sigma, mu1, mu2)
+  GradVecs gf{};
+  gf.v[0] = sg; gf.v[1] = mu1; gf.v[2] = mu2;
+  k_pack_g<<<lb_div_up(Npad, 256), 256, 0, c->stream>>>(N, Npad, 3, c->w, gf, packed);
+  LB_LAUNCH(c);
+  {
+    ProfScope prof(c, LB_PROF_SHAPE, N * N);
+    k_grad_fwd<<<dim3((unsigned)ntb, (unsigned)nsplit), GR_NTH, 0, c->stream>>>(
+        N, c->np, c->pos64, c->nrm64, packed, fflags, ntiles, c->row_ptr, c->near_patch, tps, part);
+    LB_LAUNCH(c);
+  }
+  lb_pair_counter += N * N;
+  k_reduce_g<<<lb_div_up(N, 256), 256, 0, c->stream>>>(N, (int)nsplit, part, nullptr, T);
+  LB_LAUNCH(c);
+  // transposed sums of a0 .. a5
+  GradVecs gt{};
+  for (int m = 0; m < 6; ++m) gt.v[m] = avs[m];
+  k_pack_g<<<lb_div_up(Npad, 256), 256, 0, c->stream>>>(N, Npad, 6, nullptr, gt, packed);
+  LB_LAUNCH(c);
+  {
+    ProfScope prof(c, LB_PROF_SHAPE, N * N);
+    k_grad_tr<<<dim3((unsigned)ntb, (unsigned)nsplit), GR_NTH, 0, c->stream>>>(
+        N, c->np, c->pos64, c->nrm64, packed, c->tflag, c->tmask, ntiles, tps, part);
+    LB_LAUNCH(c);
+  }
+  lb_pair_counter += N * N;
+  k_reduce_g<<<lb_div_up(N, 256), 256, 0, c->stream>>>(N, (int)nsplit, part, c->w, U);
+  LB_LAUNCH(c);
+  k_grad_combine<<<lb_div_up(N, 256), 256, 0, c->stream>>>(N, ab, T, U, grad);
+  LB_LAUNCH(c);
+  return LB_OK;
+}

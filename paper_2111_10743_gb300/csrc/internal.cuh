@@ -123,6 +123,7 @@ struct lb_ctx {
   DevBuf ws_dlow;                   // float32 / double-float copies of correction densities
   DevBuf ws_a1;                     // A1 apply: surface gradients and vector single layers
   DevBuf ws_adj;                    // transposed applies
+  DevBuf ws_shape, ws_grad;         // node-position gradient: solves, then its pair sums
   double* phi0 = nullptr;           // S[1] for A1's S W S term, in pair precision phi0_prec
   int phi0_prec = -1;
   double* host_pinned = nullptr;  // pinned scalars for GMRES control [LB_PINNED_DOUBLES]
@@ -205,6 +206,10 @@ int lb_apply_st_dev(lb_ctx* c, const double* y, double* out);
 // A3^T or A2^T by the context's formulation
 int lb_apply_at_op(lb_ctx* c, const double* y, double* out);
 int lb_build_transpose(lb_ctx* c);
+// node-position gradient of an A3-solve loss from sigma, S' sigma, S sigma,
+// S^T g_u and z = A3^-T S^T S^T g_u (device, float64); grad [N][3]
+int lb_shape_grad_pairs(lb_ctx* c, const double* gu, const double* sg, const double* mu1, const double* mu2,
+                        const double* q1, const double* z, double* grad);
 void lb_free_transpose(lb_ctx* c);
 int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out);
 // float32 hi / lo copies of the correction weights (no-op when present)

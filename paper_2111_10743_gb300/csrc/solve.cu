@@ -1446,3 +1446,81 @@ extern "C" int lb_solve_lb_adjoint(lb_ctx* c, int nrhs, const double* gu, double
   }
   return LB_OK;
 }
+
+// Node-position gradient of a loss of the A3 solve: sigma from A3 sigma = P f,
+// z from A3^T z = S^T S^T g_u (both float64 GMRES), then the gradient pair
+// sums of the adjoint module.
+extern "C" int lb_shape_gradient(lb_ctx* c, int nrhs, const double* f, const double* gu, double* grad,
+                                 lb_solve_info* info) {
+  LB_CHECK(lb_require_corr(c));
+  if (c->params.formulation != LB_A3) return lb_fail(c, LB_EINVAL, "the node-position gradient takes the A3 formulation");
+  if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
+  if (!gu) return lb_fail(c, LB_EINVAL, "null input pointer");
+  LB_CUDA(c, cudaSetDevice(c->device));
+  const int64_t N = c->N;
+  if (info) {
+    *info = lb_solve_info{};
+    info->converged = 1;
+    info->nrhs = nrhs;
+  }
+  lb_pair_counter = 0;
+  lb_apply64_counter = lb_apply32_counter = 0;
+  const double* df;
+  double* dgrad;
+  LB_CHECK(lb_stage_in(c, f, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&df));
+  LB_CHECK(lb_stage_out(c, grad, 3 * nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dgrad));
+  const bool gu_dev = lb_is_device_ptr(gu);
+  // b, sigma, potentials [4], q1, t2, z, staged g_u
+  LB_CHECK(lb_ensure(c, c->ws_shape, (size_t)(11 * N) * sizeof(double)));
+  double* b = (double*)c->ws_shape.p;
+  double* sg = b + N;
+  double* pot = sg + N;
+  double* q1 = pot + 4 * N;
+  double* t2 = q1 + N;
+  double* z = t2 + N;
+  double* gus = z + N;
+  const double* mu2 = pot + (int64_t)LB_K_S * N;
+  const double* mu1 = pot + (int64_t)LB_K_SP * N;
+  for (int r = 0; r < nrhs; ++r) {
+    const double* gr = gu + (int64_t)r * N;
+    if (!gu_dev) {
+      LB_CUDA(c, cudaMemcpyAsync(gus, gr, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      gr = gus;
+    }
+    double removed = 0;
+    LB_CHECK(project_mean_zero(c, df + (int64_t)r * N, b, &removed));
+    if (info && r == 0) info->removed_mean = removed;
+    int it1 = 0, it2 = 0;
+    double res1 = 0, res2 = 0;
+    std::vector<double> hist;
+    LB_CHECK(gmres(c, LB_FP64, b, sg, c->params.tol, c->params.max_iter, &it1, &res1, r == 0 ? &hist : nullptr));
+    LB_CHECK(lb_potentials(c, LB_FP64, sg, pot, (1u << LB_K_S) | (1u << LB_K_SP)));
+    LB_CHECK(lb_apply_st_dev(c, gr, q1));
+    LB_CHECK(lb_apply_st_dev(c, q1, t2));
+    c->adjoint = true;
+    const int rc = gmres(c, LB_FP64, t2, z, c->params.tol, c->params.max_iter, &it2, &res2, nullptr);
+    c->adjoint = false;
+    LB_CHECK(rc);
+    LB_CHECK(lb_shape_grad_pairs(c, gr, sg, mu1, mu2, q1, z, dgrad + (int64_t)r * 3 * N));
+    if (info) {
+      info->iterations += it1 + it2;
+      const double res = std::max(res1, res2);
+      info->converged = info->converged && (res < c->params.tol);
+      info->rel_residual = std::max(info->rel_residual, res);
+      if (r == 0) {
+        info->history_len = (int32_t)std::min<size_t>(hist.size(), 128);
+        for (int i = 0; i < info->history_len; ++i) info->history[i] = hist[i];
+      }
+    }
+  }
+  LB_CHECK(lb_stage_out_finish(c, grad, dgrad, 3 * nrhs * N * sizeof(double)));
+  if (info) {
+    info->pairs = lb_pair_counter;
+    info->applies_fp64 = lb_apply64_counter;
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (!info->converged)
+      return lb_fail(c, LB_ENOTCONVERGED, "a GMRES of the gradient did not reach tol %.3g (residual %.3g)",
+                     c->params.tol, info->rel_residual);
+  }
+  return LB_OK;
+}

@@ -104,3 +104,27 @@ def test_adjoint_refuses_A1(lb):
     with pytest.raises(lb.LBError) as e:
         ctx.apply_At(np.zeros((1, d.geo.N)))
     assert e.value.code == lb.LB_EINVAL
+
+
+@pytest.mark.parametrize("name", ["sphere300", "ellipsoid1200"])
+def test_shape_gradient_matches_oracle(lb, name):
+    """Node-position gradient of an A3-solve loss (corrections held fixed)
+    against the oracle's dense gradient, which its own pin checks against
+    central differences."""
+    from oracle.shape import shape_gradient_A3
+    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3, precision=lb.LB_FP64, tol=1e-14)
+    N = d.geo.N
+    rng = np.random.default_rng(43)
+    f = rng.standard_normal((2, N))
+    gu = rng.standard_normal((2, N))
+    grad, info = ctx.shape_gradient(f, gu)
+    assert grad.shape == (2, N, 3)
+    assert info["converged"] and info["iterations"] > 0
+    for r in range(2):
+        ref = shape_gradient_A3(d, f[r], gu[r])
+        assert _rel(grad[r], ref) < 1e-9
+    if name == "sphere300":
+        ctx2, _, _ = ctx_for(lb, name, formulation=lb.LB_A2, precision=lb.LB_FP64)
+        with pytest.raises(lb.LBError) as e:
+            ctx2.shape_gradient(f[:1], gu[:1])
+        assert e.value.code == lb.LB_EINVAL
