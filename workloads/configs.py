@@ -10,6 +10,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+from . import implicit as I
 from . import rhs as R
 from . import surfaces as S
 
@@ -61,6 +62,34 @@ def torus_batch(n_theta: int = 32, n_phi: int = 32, order: int = 6, nrand: int =
     return Workload(f"torus-{n_theta}x{n_phi}-k{order}", s, f, extra={"F": F})
 
 
+def _centred(surf: S.Surface):
+    """Node positions about the bounding-box centre, and the box's half-extent."""
+    lo, hi = surf.X.min(axis=0), surf.X.max(axis=0)
+    return surf.X - 0.5 * (lo + hi)[None, :], 0.5 * float(np.max(hi - lo))
+
+
+def genus2_autograd(h: float = 0.135, order: int = 6, seed: int = 1004) -> Workload:
+    """Two blended tori (genus 2), about 4,000 order-6 patches: one random
+    Legendre f and a Legendre target u_t for the loss |u - u_t|^2."""
+    s = I.tori_chain(2, h, order)
+    rng = np.random.default_rng(seed)
+    Xc, L = _centred(s)
+    f = R.legendre_field(Xc, rng, 4, L)
+    ut = R.legendre_field(Xc, rng, 4, L)
+    return Workload(f"tori2-h{h:g}-k{order}", s, f[None, :], extra={"u_target": ut})
+
+
+def genus5_batch(h: float = 0.07, order: int = 6, nF: int = 5, nrand: int = 22, seed: int = 1005) -> Workload:
+    """Five blended tori (genus 5), about 36,000 order-6 patches: nF random
+    tangential fields F (2 nF Hodge solves) and nrand random Legendre f."""
+    s = I.tori_chain(5, h, order)
+    rng = np.random.default_rng(seed)
+    Xc, L = _centred(s)
+    F = np.stack([_tangential(s, R.legendre_field(Xc, rng, 4, L, ncomp=3)) for _ in range(nF)])
+    f = np.stack([R.legendre_field(Xc, rng, 4, L) for _ in range(nrand)])
+    return Workload(f"tori5-h{h:g}-k{order}", s, f, tol=1e-9, extra={"F": F})
+
+
 # the configurations of the scope table, by index
 def config(index: int) -> Workload:
     if index == 1:
@@ -69,4 +98,8 @@ def config(index: int) -> Workload:
         return ellipsoid_gauss(3, 8, 1002)
     if index == 3:
         return torus_batch(32, 32, 6, 16, 1003)
+    if index == 4:
+        return genus2_autograd(0.135, 6, 1004)
+    if index == 5:
+        return genus5_batch(0.07, 6, 5, 22, 1005)
     raise ValueError(f"configuration {index} is not built")
