@@ -7,6 +7,8 @@ oracle's geometry on them by the Gauss-Bonnet theorem (the integral of K is
 2 pi (2 - 2g)) and by the closed-form mean curvature of a level set.  The
 curvature formulas themselves are pinned on a plain torus, whose curvatures
 are known in closed form, and against finite differences of the unit normal.
+The oracle's layer potentials on the genus-2 surface meet the Gauss and
+Green identities at sampled targets.
 """
 import numpy as np
 import pytest
@@ -148,3 +150,35 @@ def test_genus2_and_genus5_workloads():
     assert I.euler_characteristic(V, T) == -2
     assert w.f.shape == (1, s.N) and w.extra["u_target"].shape == (s.N,)
     assert np.isfinite(w.f).all()
+
+
+def test_green_and_gauss_identities_on_genus2_sampled_rows():
+    """Oracle layer potentials on the genus-2 surface at 12 sampled targets:
+    Gauss D[1] = -1/2 and Green S[dU/dn] - D[U] = U/2 for U = 1/|x - x0|,
+    x0 at the centre of a hole (outside the solid, so U is harmonic inside).
+    Both converge with the order (discretisation error, not parity)."""
+    from oracle import farsum
+    from oracle.geometry import build_geometry, near_lists
+    from oracle.quadrature import build_corrections
+    errs = []
+    for order in (4, 6):
+        s = I.tori_chain(2, 0.2, order)
+        g = build_geometry(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv)
+        ptr, pl = near_lists(g, 2.0)
+        rows = np.sort(np.random.default_rng(7).choice(g.N, 12, replace=False))
+        vals, _ = build_corrections(g, ptr, pl, eps_q=1e-12, rows=rows)
+        d = g.X - np.array([0.0, 0.0, 0.0])[None, :]
+        r = np.linalg.norm(d, axis=1)
+        U, dU, one = 1 / r, -np.einsum("ij,ij->i", d, g.n) / r ** 3, np.ones(g.N)
+        far = farsum.far_sums(g, ptr, pl, np.stack([dU, U, one]), targets=rows)
+
+        def near(K, sig):
+            out = []
+            for i in rows:
+                out.append(sum(vals[b, K] @ sig[pl[b] * g.np_:(pl[b] + 1) * g.np_] for b in range(ptr[i], ptr[i + 1])))
+            return np.array(out)
+
+        green = far[0, 0] + near(0, dU) - far[1, 1] - near(1, U) - 0.5 * U[rows]
+        gauss = far[2, 1] + near(1, one) + 0.5
+        errs.append(max(np.abs(green).max(), np.abs(gauss).max()))
+    assert errs[1] < 1e-5 and errs[1] < errs[0] / 5
