@@ -15,6 +15,9 @@ import os
 
 import numpy as np
 
+from . import checkpoint as _checkpoint
+from .checkpoint import CheckpointError
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libgblb.so")
 
@@ -222,6 +225,8 @@ class Context:
         args = [_ptr(a, np.float64) for a in (ref_uv, ref_w, X, Xu, Xv)]
         self._check(_lib.lb_upload_geometry(self._h, int(npatch), int(order), *[a[0] for a in args]))
         self.N = self.info()["N"]
+        host = [a.detach().cpu().numpy() if hasattr(a, "detach") else a for a in (ref_uv, ref_w, X, Xu, Xv)]
+        self._digest = _checkpoint.geometry_digest(npatch, order, *host)
 
     def upload_surface(self, surf):
         """Convenience: upload a workloads.surfaces.Surface-like object."""
@@ -262,6 +267,25 @@ class Context:
                                             ctypes.c_void_p(pa.ctypes.data),
                                             ctypes.c_void_p(vals.ctypes.data) if with_vals else None))
         return rp, pa, vals
+
+    def geometry_digest(self) -> str:
+        """SHA-256 of the geometry inputs, taken when they were uploaded."""
+        if getattr(self, "_digest", None) is None:
+            raise LBError(LB_EINVAL, "no geometry uploaded")
+        return self._digest
+
+    def save_corrections(self, path):
+        """Write the corrections with the geometry digest and parameters (.npz)."""
+        p = self.get_params()
+        rp, pa, vals = self.get_corrections()
+        _checkpoint.save(path, self.geometry_digest(), p.near_factor, p.eps_quad, rp, pa, vals)
+
+    def load_corrections_file(self, path):
+        """Load corrections saved for this geometry and these parameters,
+        in place of build_corrections; CheckpointError on any mismatch."""
+        p = self.get_params()
+        rp, pa, vals = _checkpoint.load(path, self.geometry_digest(), p.near_factor, p.eps_quad)
+        self.load_corrections(rp, pa, vals)
 
     # --- applies -------------------------------------------------------
     def _nrhs(self, x, per=1):
