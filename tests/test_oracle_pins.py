@@ -303,15 +303,18 @@ def test_sphere_solve_converges_at_high_order(k):
     refinement (the paper reports O(h^(p+1/2)), p = k + 1, asymptotically).
     One subdivision of the 20-patch icosphere halves h; these coarse levels
     are pre-asymptotic, measured ratios 13.2 (k = 3) and 21.8 (k = 4), so
-    the pin is a rate of at least k."""
-    errs = []
+    the pin is a rate of at least k.  The GMRES iteration count does not
+    grow with the refinement (second kind, Section 6.2)."""
+    errs, its = [], []
     for level in (0, 1):
         s = S.icosphere(level, k)
         d = discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0, eps_q=1e-12, workers=WORKERS)
         f = y32(s.X)
-        u, *_ = solve_lb(d, f, "A3", tol=1e-13)
+        u, _, it, _ = solve_lb(d, f, "A3", tol=1e-13)
         errs.append(np.abs(u + f / 12).max())
+        its.append(it)
     assert errs[0] / errs[1] > 2.0 ** k
+    assert its[1] <= its[0] + 1, its
 
 
 def test_manufactured_ellipsoid(ellipsoid):
