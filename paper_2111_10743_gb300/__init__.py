@@ -411,6 +411,39 @@ def _torch_fns():
             ctx.ctx_lb.solve_lb_adjoint(gu.contiguous(), out=gf)
             return gf, None
 
+    class SolveLBShape(torch.autograd.Function):
+        """u = solve_lb(f) differentiable in f and in the node positions X.
+
+        X: float64 tensor [N, 3] holding the positions uploaded to ctx_lb
+        (it stands for them; the solve reads the context's copy).  Its
+        gradient is the library's node-position gradient with the
+        corrections, w, n and H held fixed, summed over the right-hand
+        sides; A3 only."""
+
+        @staticmethod
+        def forward(ctx, f, X, ctx_lb):
+            u = torch.empty_like(f)
+            fd = f.detach().contiguous()
+            ctx_lb.solve_lb(fd, out=u)
+            ctx.ctx_lb = ctx_lb
+            ctx.save_for_backward(fd)
+            ctx.x_shape = X.shape
+            return u
+
+        @staticmethod
+        def backward(ctx, gu):
+            (f,) = ctx.saved_tensors
+            gu = gu.contiguous()
+            gf = gX = None
+            if ctx.needs_input_grad[0]:
+                gf = torch.empty_like(gu)
+                ctx.ctx_lb.solve_lb_adjoint(gu, out=gf)
+            if ctx.needs_input_grad[1]:
+                g = torch.empty(gu.shape + (3,), dtype=gu.dtype, device=gu.device)
+                ctx.ctx_lb.shape_gradient(f, gu, out=g)
+                gX = g.sum(dim=0).reshape(ctx.x_shape)
+            return gf, gX, None
+
     class ApplyA(torch.autograd.Function):
         """y = A tau with gradient A^T g_y."""
 
@@ -427,12 +460,17 @@ def _torch_fns():
             ctx.ctx_lb.apply_At(gy.contiguous(), out=gt)
             return gt, None
 
-    return SolveLB, ApplyA
+    return SolveLB, ApplyA, SolveLBShape
 
 
-def solve_lb_autograd(f, ctx_lb):
-    """Differentiable mean-zero Laplace-Beltrami solve (A3 or A2): u = solve(f)."""
-    return _torch_fns()[0].apply(f, ctx_lb)
+def solve_lb_autograd(f, ctx_lb, X=None):
+    """Differentiable mean-zero Laplace-Beltrami solve (A3 or A2): u = solve(f).
+
+    With X (a tensor [N, 3] standing for the uploaded node positions) the
+    solve is also differentiable in X (A3; corrections held fixed)."""
+    if X is None:
+        return _torch_fns()[0].apply(f, ctx_lb)
+    return _torch_fns()[2].apply(f, X, ctx_lb)
 
 
 def apply_A_autograd(tau, ctx_lb):

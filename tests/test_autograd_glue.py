@@ -1,0 +1,84 @@
+"""The torch.autograd wrappers' plumbing, on the CPU.
+
+A stand-in context answers solve_lb, solve_lb_adjoint and shape_gradient
+from the oracle's dense FP64 matrices, so these tests check only what the
+wrappers add: which calls the backward pass makes, the sum of the
+node-position gradient over right-hand sides, and the shapes.  The library
+calls themselves are checked against the oracle on the GPU.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+class OracleContext:
+    def __init__(self, disc):
+        from oracle.gmres import dense_matrix
+        self.d = disc
+        N = disc.geo.N
+        self.S = dense_matrix(lambda x: disc.S(x), N)
+        self.A = dense_matrix(lambda x: disc.apply("A3", x), N)
+        w = disc.geo.w
+        self.P = np.eye(N) - np.outer(np.ones(N), w) / w.sum()
+        self.L = self.S @ self.S @ np.linalg.solve(self.A, self.P)   # u = L f
+        self.calls = []
+        self.cache = {}
+
+    def solve_lb(self, f, out):
+        self.calls.append("solve")
+        out.copy_(torch.from_numpy(f.numpy() @ self.L.T))
+
+    def solve_lb_adjoint(self, gu, out):
+        self.calls.append("adjoint")
+        out.copy_(torch.from_numpy(gu.numpy() @ self.L))
+
+    def grad(self, f, gu):
+        """The oracle's node-position gradient, cached per input pair."""
+        from oracle.shape import shape_gradient_A3
+        key = (f.tobytes(), gu.tobytes())
+        if key not in self.cache:
+            self.cache[key] = shape_gradient_A3(self.d, f, gu)
+        return self.cache[key]
+
+    def shape_gradient(self, f, gu, out):
+        self.calls.append("shape")
+        for r in range(f.shape[0]):
+            out[r] = torch.from_numpy(self.grad(f[r].numpy(), gu[r].numpy()))
+
+
+@pytest.fixture(scope="module")
+def octx():
+    from workloads.configs import config
+    from oracle.layers import discretise
+    s = config(1).surface
+    return OracleContext(discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0, eps_q=1e-12))
+
+
+def test_solve_autograd_density_and_positions(octx):
+    import paper_2111_10743_gb300 as lb
+    N = octx.d.geo.N
+    rng = np.random.default_rng(45)
+    f = torch.tensor(rng.standard_normal((2, N)), requires_grad=True)
+    X = torch.tensor(octx.d.geo.X.copy(), requires_grad=True)
+    ut = torch.tensor(rng.standard_normal((2, N)))
+    octx.calls.clear()
+    u = lb.solve_lb_autograd(f, octx, X=X)
+    loss = ((u - ut) ** 2).sum()
+    loss.backward()
+    assert octx.calls == ["solve", "adjoint", "shape"]
+    gu = 2.0 * (u.detach() - ut).numpy()
+    assert np.allclose(f.grad.numpy(), gu @ octx.L, rtol=0, atol=1e-12)
+    ref = sum(octx.grad(f.detach()[r].numpy(), gu[r]) for r in range(2))
+    assert X.grad.shape == (N, 3)
+    assert np.abs(X.grad.numpy() - ref).max() < 1e-12 * np.abs(ref).max()
+    # positions only: no adjoint solve for f
+    octx.calls.clear()
+    f2 = f.detach()[:1]
+    (lb.solve_lb_autograd(f2, octx, X=X) ** 2).sum().backward()
+    assert octx.calls == ["solve", "shape"]
+    # without X the wrapper is the density-only one
+    octx.calls.clear()
+    g = torch.tensor(rng.standard_normal((1, N)), requires_grad=True)
+    (lb.solve_lb_autograd(g, octx) ** 2).sum().backward()
+    assert octx.calls == ["solve", "adjoint"]
