@@ -347,6 +347,44 @@ int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, const double* n
  * check harmonic fields (div H = 0). */
 int lb_surface_div(lb_ctx* ctx, int nrhs, const double* F, double* out);
 
+/* Octree plan for a fast-multipole far field (host only: no context, no
+ * device work; not in the paper, which evaluates its layer potentials with
+ * an external FMM library, Section 4.1).  The classical uniform-depth
+ * scheme of Greengard and Rokhlin: boxes of level l are the occupied cells
+ * of a 2^l grid over a cube holding every node; U(leaf) = the adjacent
+ * leaves, itself included; V(box) = the children of the boxes adjacent to
+ * its parent that are not adjacent to it (levels >= 2).  For any two
+ * leaves exactly one holds: one is in the other's U list, or at exactly
+ * one level their ancestors are in each other's V lists.  With a leaf side
+ * of at least (near_factor + 1) max_P R_P every near (node, patch) pair lies
+ * in adjacent leaves.
+ * lb_fmm_plan_create: X [n][3] host float64; the depth is the largest
+ *   d <= max_depth (<= 20) whose leaf side (cube side / 2^d) is at least
+ *   min_leaf_side.  LB_EINVAL for n < 1, a non-finite coordinate or bad
+ *   arguments (message via lb_last_error(NULL)); LB_ENOMEM.
+ * lb_fmm_plan_arrays copies (any pointer may be NULL; host int64):
+ *   perm [n]: node ids in Morton order (ties by id);
+ *   level_ptr [depth+2]: boxes of level l are [level_ptr[l], level_ptr[l+1]);
+ *   box_key [nbox]: Morton key (x bit 0, y bit 1, z bit 2, ...) within the
+ *     level, ascending per level; box_parent [nbox] (-1 at level 0);
+ *   node_ptr [nleaf+1]: leaf b holds perm[node_ptr[b] .. node_ptr[b+1]);
+ *   u_ptr [nleaf+1], u_idx [nu]: U lists as leaf indices (b - level_ptr[depth]);
+ *   v_ptr [nbox+1], v_idx [nv]: V lists as box indices.
+ * The plan owns its arrays until lb_fmm_plan_destroy (accepts NULL). */
+typedef struct lb_fmm_plan lb_fmm_plan;
+typedef struct {
+  int32_t depth;
+  int64_t n, nbox, nleaf, nu, nv;
+  double lo[3];   /* cube corner */
+  double side;    /* cube side */
+} lb_fmm_info;
+int lb_fmm_plan_create(int64_t n, const double* X, double min_leaf_side, int max_depth, lb_fmm_plan** out);
+int lb_fmm_plan_info(const lb_fmm_plan* plan, lb_fmm_info* info);
+int lb_fmm_plan_arrays(const lb_fmm_plan* plan, int64_t* perm, int64_t* level_ptr, int64_t* box_key,
+                       int64_t* box_parent, int64_t* node_ptr, int64_t* u_ptr, int64_t* u_idx,
+                       int64_t* v_ptr, int64_t* v_idx);
+int lb_fmm_plan_destroy(lb_fmm_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

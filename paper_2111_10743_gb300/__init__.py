@@ -102,6 +102,10 @@ def _load():
         "lb_solve_lb_adjoint": [P, ctypes.c_int, P, P, P],
         "lb_shape_gradient": [P, ctypes.c_int, P, P, P, P],
         "lb_far_sums_noalloc": [ctypes.c_int64, ctypes.c_int, P, P, P, P, P, P, P, P],
+        "lb_fmm_plan_create": [ctypes.c_int64, P, ctypes.c_double, ctypes.c_int, P],
+        "lb_fmm_plan_info": [P, P],
+        "lb_fmm_plan_arrays": [P, P, P, P, P, P, P, P, P, P],
+        "lb_fmm_plan_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -385,6 +389,40 @@ class Context:
         info = lb_solve_info()
         self._check(_lib.lb_harmonic_fields(self._h, nF, p, o, ctypes.byref(info)))
         return res, info.as_dict()
+
+
+class lb_fmm_info(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("n", ctypes.c_int64), ("nbox", ctypes.c_int64),
+                ("nleaf", ctypes.c_int64), ("nu", ctypes.c_int64), ("nv", ctypes.c_int64),
+                ("lo", ctypes.c_double * 3), ("side", ctypes.c_double)]
+
+
+def fmm_plan(X, min_leaf_side: float, max_depth: int = 20) -> dict:
+    """Octree plan of the nodes X [n, 3] (lb_fmm_plan_create; host only).
+
+    Returns depth, the cube (lo, side) and the arrays perm, level_ptr,
+    box_key, box_parent, node_ptr, u_ptr, u_idx, v_ptr, v_idx."""
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    h = ctypes.c_void_p()
+    rc = _lib.lb_fmm_plan_create(X.shape[0], ctypes.c_void_p(X.ctypes.data), float(min_leaf_side),
+                                 int(max_depth), ctypes.byref(h))
+    if rc != LB_OK:
+        raise LBError(rc, _lib.lb_last_error(None).decode())
+    try:
+        inf = lb_fmm_info()
+        _lib.lb_fmm_plan_info(h, ctypes.byref(inf))
+        d = inf.depth
+        out = {"depth": d, "lo": np.array(inf.lo[:]), "side": inf.side,
+               "perm": np.empty(inf.n, np.int64), "level_ptr": np.empty(d + 2, np.int64),
+               "box_key": np.empty(inf.nbox, np.int64), "box_parent": np.empty(inf.nbox, np.int64),
+               "node_ptr": np.empty(inf.nleaf + 1, np.int64), "u_ptr": np.empty(inf.nleaf + 1, np.int64),
+               "u_idx": np.empty(inf.nu, np.int64), "v_ptr": np.empty(inf.nbox + 1, np.int64),
+               "v_idx": np.empty(inf.nv, np.int64)}
+        names = ("perm", "level_ptr", "box_key", "box_parent", "node_ptr", "u_ptr", "u_idx", "v_ptr", "v_idx")
+        _lib.lb_fmm_plan_arrays(h, *[ctypes.c_void_p(out[k].ctypes.data) for k in names])
+        return out
+    finally:
+        _lib.lb_fmm_plan_destroy(h)
 
 
 # --- autograd ---------------------------------------------------------------
