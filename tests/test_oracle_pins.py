@@ -458,3 +458,35 @@ def test_shape_gradient_matches_finite_differences(cfg1):
     Lm = loss(dataclasses.replace(d, geo=dataclasses.replace(g, X=g.X - h * dX)))[0]
     an = np.sum(grad * dX)
     assert abs((Lp - Lm) / (2 * h) - an) < 1e-7 * abs(an)
+
+
+def test_planted_missing_SD_gradient_breaks_finite_differences(cfg1, monkeypatch):
+    """Dropping the S''+D' kernel's gradient from the node-position gradient
+    moves its directional derivative far outside the central-difference pin."""
+    import dataclasses
+    from oracle import shape as Sh
+    from oracle.gmres import solve_lb
+    w_, d = cfg1
+    g = d.geo
+    rng = np.random.default_rng(3)
+    f = w_.f[0] + 0.3 * rng.standard_normal(g.N)
+    ut = rng.standard_normal(g.N)
+
+    def loss(dd):
+        u, *_ = solve_lb(dd, f, "A3", tol=1e-14)
+        return 0.5 * np.sum((u - ut) ** 2), u
+
+    _, u0 = loss(d)
+    dX = rng.standard_normal((g.N, 3))
+    h = 1e-5
+    Lp = loss(dataclasses.replace(d, geo=dataclasses.replace(g, X=g.X + h * dX)))[0]
+    Lm = loss(dataclasses.replace(d, geo=dataclasses.replace(g, X=g.X - h * dX)))[0]
+    fd = (Lp - Lm) / (2 * h)
+    orig = Sh.kernel_gradients
+
+    def planted(disc):
+        GS, GSp, GSD = orig(disc)
+        return GS, GSp, 0.0 * GSD
+    monkeypatch.setattr(Sh, "kernel_gradients", planted)
+    an = np.sum(Sh.shape_gradient_A3(d, f, u0 - ut) * dX)
+    assert abs(fd - an) > 1e-2 * abs(fd)
