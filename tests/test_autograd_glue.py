@@ -49,10 +49,10 @@ class OracleContext:
 
 @pytest.fixture(scope="module")
 def octx():
-    from workloads.configs import config
+    from workloads import surfaces as S
     from oracle.layers import discretise
-    s = config(1).surface
-    return OracleContext(discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0, eps_q=1e-12))
+    s = S.icosphere(0, 3)   # 20 patches of order 3, N = 200
+    return OracleContext(discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0, eps_q=1e-10))
 
 
 def test_solve_autograd_density_and_positions(octx):
