@@ -1,4 +1,5 @@
-// Transposed applies and the adjoint (density) solve.
+// Transposed applies, the adjoint (density) solve and the pair sums of the
+// node-position gradient (at the end of this file).
 //
 // The discrete operators are matrices: S_ij = w_j G(x_i, x_j) for far pairs
 // (patch(j) not in Near(i)) plus the correction weights C_ij for near ones,

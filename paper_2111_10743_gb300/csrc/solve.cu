@@ -1,6 +1,7 @@
 // GMRES, the mean-zero Laplace-Beltrami solve (single and lockstep), mixed-
 // precision refinement, surface differential operators, harmonic vector
-// fields, the A1 apply and the adjoint solve.
+// fields, the A1 apply, the adjoint solve and the node-position gradient
+// (whose pair sums live in the adjoint module).
 //
 // GMRES (Section 6: relative residual below tol, at most max_iter = 100
 // iterations): x0 = 0, no restart, Euclidean inner product.  The Arnoldi
