@@ -150,6 +150,10 @@ def test_genus2_and_genus5_workloads():
     assert I.euler_characteristic(V, T) == -2
     assert w.f.shape == (1, s.N) and w.extra["u_target"].shape == (s.N,)
     assert np.isfinite(w.f).all()
+    # the genus-5 workload's mesh (its charts and data take about 20 s more)
+    V, T = I.mesh(I.ToriChain(5), 0.07)
+    assert 34000 <= len(T) <= 38000
+    assert I.is_closed_manifold(len(V), T) and I.euler_characteristic(V, T) == -8
 
 
 def test_green_and_gauss_identities_on_genus2_sampled_rows():
