@@ -490,3 +490,120 @@ def test_planted_missing_SD_gradient_breaks_finite_differences(cfg1, monkeypatch
     monkeypatch.setattr(Sh, "kernel_gradients", planted)
     an = np.sum(Sh.shape_gradient_A3(d, f, u0 - ut) * dX)
     assert abs(fd - an) > 1e-2 * abs(fd)
+
+
+# --- near weights on flat patches against closed forms ------------------------
+
+def _flat_patches(order, tris):
+    uv, w = node_rule(order)
+    X, Xu, Xv = [], [], []
+    for A, B, C in tris:
+        A, B, C = (np.asarray(v, dtype=np.float64) for v in (A, B, C))
+        X.append(A[None] + uv[:, :1] * (B - A)[None] + uv[:, 1:] * (C - A)[None])
+        Xu.append(np.tile(B - A, (len(uv), 1)))
+        Xv.append(np.tile(C - A, (len(uv), 1)))
+    return build_geometry(order, uv, w, np.concatenate(X), np.concatenate(Xu), np.concatenate(Xv))
+
+
+def _single_layer_in_plane(x, tri, p0, g, Q):
+    """(1/4 pi) int_T p(y) / |x - y| dA for x inside the flat triangle T and
+    p(y) = p0 + g.(y - x) + (y - x)^T Q (y - x).  In polar coordinates about
+    x the radial integral is elementary; across the edge at distance h with
+    foot f and unit tangent t (counterclockwise), the angle phi from the
+    perpendicular has R = h sec(phi), and the sec^k integrals are
+    asinh(tan), sec and (sec tan - asinh(tan)) / 2."""
+    A, B, C = (np.asarray(v, dtype=np.float64) for v in tri)
+    n = np.cross(B - A, C - A)
+    n /= np.linalg.norm(n)
+    tot = 0.0
+    for a, b in ((A, B), (B, C), (C, A)):
+        t = (b - a) / np.linalg.norm(b - a)
+        f = a + np.dot(x - a, t) * t
+        h = np.linalg.norm(f - x)
+        nu = (f - x) / h
+        assert np.allclose(np.cross(n, nu), t)
+        sa, sb = np.dot(a - f, t) / h, np.dot(b - f, t) / h
+        ash = np.arcsinh(sb) - np.arcsinh(sa)
+        sec = np.hypot(1.0, sb) - np.hypot(1.0, sa)
+        sectan = np.hypot(1.0, sb) * sb - np.hypot(1.0, sa) * sa
+        tot += p0 * h * ash
+        tot += 0.5 * h ** 2 * (g @ nu * ash + g @ t * sec)
+        tot += h ** 3 / 3.0 * (nu @ Q @ nu * ash + 2.0 * (nu @ Q @ t) * sec + (t @ Q @ t) * 0.5 * (sectan - ash))
+    return tot / (4.0 * np.pi)
+
+
+def _solid_angle(x, tri):
+    """Signed solid angle of the triangle seen from x (Van Oosterom and
+    Strackee 1983), positive when x lies behind the oriented triangle."""
+    R = [np.asarray(v, dtype=np.float64) - x for v in tri]
+    r = [np.linalg.norm(v) for v in R]
+    num = R[0] @ np.cross(R[1], R[2])
+    den = r[0] * r[1] * r[2] + (R[0] @ R[1]) * r[2] + (R[0] @ R[2]) * r[1] + (R[1] @ R[2]) * r[0]
+    return 2.0 * np.arctan2(num, den)
+
+
+def _layer_by_dblquad(x, nx, tri, K, p):
+    """(1/4 pi) int_T K(x, y) p(y) dA by scipy's adaptive dblquad (x off T)."""
+    from scipy import integrate
+    A, B, C = (np.asarray(v, dtype=np.float64) for v in tri)
+    e1, e2 = B - A, C - A
+    ny = np.cross(e1, e2)
+    J = np.linalg.norm(ny)
+    ny /= J
+
+    def f(v, u):
+        y = A + u * e1 + v * e2
+        d = x - y
+        r = np.linalg.norm(d)
+        if K == 0:
+            k = 1.0 / r
+        elif K == 1:
+            k = (ny @ d) / r ** 3
+        elif K == 2:
+            k = -(nx @ d) / r ** 3
+        else:
+            e = nx - ny
+            k = (3.0 * (nx @ d) * (e @ d) / r ** 2 - 0.5 * (e @ e)) / r ** 3
+        return k * p(y) * J / (4.0 * np.pi)
+    return integrate.dblquad(f, 0.0, 1.0, 0.0, lambda u: 1.0 - u, epsabs=1e-14, epsrel=1e-12)[0]
+
+
+def test_near_weights_on_flat_patches_match_closed_forms():
+    """Flat triangles make the near-field integrals exact references
+    (Section 4's corrections reproduce polynomial densities of degree <= k):
+    self blocks against the polar closed form of the single layer (D, S' and
+    S''+D' vanish in the plane), near blocks against the solid angle (D of a
+    constant) and against scipy's adaptive dblquad (all four kernels)."""
+    from oracle.geometry import near_lists
+    T0 = ((0.0, 0.0, 0.0), (1.0, 0.0, 0.0), (0.2, 0.9, 0.0))
+    T1 = ((0.1, 0.1, 0.25), (0.9, 0.2, 0.45), (0.3, 0.8, 0.3))
+    g = _flat_patches(4, [T0, T1])
+    npn = g.np_
+    ptr, pl = near_lists(g, 2.0)
+    rows = np.concatenate([np.arange(npn), npn + np.arange(0, npn, 3)])
+    vals, _ = build_corrections(g, ptr, pl, eps_q=1e-12, rows=rows)
+    gv = np.array([0.3, -0.7, 0.0])
+    Q = np.array([[0.8, 0.3, 0.0], [0.3, -0.5, 0.0], [0.0, 0.0, 0.0]])
+    y = g.X[:npn]
+    nnear = 0
+    for i in rows:
+        blk = [b for b in range(ptr[i], ptr[i + 1]) if pl[b] == 0]
+        if not blk:
+            continue
+        b = blk[0]
+        if i < npn:   # self block
+            d = y - g.X[i]
+            p = 1.3 + d @ gv + np.einsum("ij,jk,ik->i", d, Q, d)
+            ref = _single_layer_in_plane(g.X[i], T0, 1.3, gv, Q)
+            assert abs(vals[b, 0] @ p - ref) < 1e-13 * abs(ref)
+            assert np.abs(vals[b, 1:]).max() < 1e-14
+        else:         # near block
+            nnear += 1
+            one = np.ones(npn)
+            assert abs(vals[b, 1] @ one + _solid_angle(g.X[i], T0) / (4.0 * np.pi)) < 1e-13
+            pq = lambda z: 1.0 + 0.5 * z[0] - z[1] ** 2 + 0.7 * z[0] * z[1]
+            p = np.array([pq(z) for z in y])
+            for K in range(4):
+                ref = _layer_by_dblquad(g.X[i], g.n[i], T0, K, pq)
+                assert abs(vals[b, K] @ p - ref) < 1e-12 * max(1.0, abs(ref)), (i, K)
+    assert nnear >= 3
