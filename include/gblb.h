@@ -173,7 +173,12 @@ int lb_build_corrections(lb_ctx* ctx);
  *   row_ptr [N+1] (int64): blocks of row i are row_ptr[i] .. row_ptr[i+1]-1,
  *   patch [nnzb] (int32): the near patch of each block, ascending per row,
  *   vals [nnzb][4][np] (float64): the weights, kernel order S, D, S', S''+D'.
- * The far-field sums skip exactly these (row, patch) pairs. */
+ * The far-field sums skip exactly these (row, patch) pairs.  The lists are
+ * checked on the device before they are kept: row_ptr must run from 0 to
+ * nnzb without decreasing, every patch index must lie in [0, npatch) and the
+ * patches of a row must be strictly ascending; LB_EINVAL otherwise (nothing is
+ * kept).  The library cannot check the size of a host vals buffer: it must
+ * hold nnzb * 4 * np doubles. */
 int lb_load_corrections(lb_ctx* ctx, int64_t nnzb, const int64_t* row_ptr,
                         const int32_t* patch, const double* vals);
 
@@ -323,7 +328,8 @@ int lb_get_tuning(lb_ctx* ctx, int* shapes);
  * a service that must keep a fixed device footprint after start-up.  No
  * context is needed.
  *   npatch, np: the surface as for lb_upload_geometry; N = npatch * np must
- *     not exceed 65,536 (LB_EINVAL otherwise, message via lb_last_error(NULL)).
+ *     not exceed 65,536 (LB_EINVAL otherwise, checked without forming the
+ *     product; message via lb_last_error(NULL)).
  *   X [N][3], nrm [N][3], w [N]: node positions, unit normals, smooth weights
  *     (device, float64; e.g. from lb_get_geometry).
  *   sigma [N]: the density (device, float64).
@@ -333,7 +339,11 @@ int lb_get_tuning(lb_ctx* ctx, int* shapes);
  *     with LB_FP32.
  *   stream: cudaStream_t for every launch (NULL = legacy default stream).
  * The first call on a device looks up the array's device address (with that
- * device current) and keeps it for the later calls.  Every
+ * device current) and keeps it for the later calls.  Under CUDA's lazy module
+ * loading (the default) that lookup is also when the array is created on the
+ * device, so the first call can fail with LB_ECUDA when the device is out of
+ * memory: make one call (any valid input) before a memory pool takes the
+ * device's memory, and before any stream capture.  Every
  * call shares the one array and overwrites it: calls that may overlap on the
  * GPU (different streams, or different host threads) race and must be
  * serialised by the caller.  Returns LB_ECUDA if the lookup or a launch
@@ -341,6 +351,15 @@ int lb_get_tuning(lb_ctx* ctx, int* shapes);
 int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, const double* nrm, const double* w,
                         const double* sigma, const int64_t* row_ptr, const int32_t* near_patch,
                         double* out, void* stream);
+
+/* Failure injection for tests (not in the paper): after `after` further
+ * device allocations by this context (0 = the very next one), one allocation
+ * fails exactly as if cudaMalloc had run out of memory, so the call making it
+ * returns LB_ENOMEM; the injection then disarms itself.  after < 0 disarms it.
+ * A workspace whose allocation failed is left empty and allocated again by
+ * the next call that needs it, so the context stays usable; a failed
+ * lb_upload_geometry leaves no geometry (upload again). */
+int lb_debug_fail_alloc(lb_ctx* ctx, int64_t after);
 
 /* Surface divergence of tangential fields F [nrhs][N][3] -> out [nrhs][N]
  * (Section 2; host or device).  Used for the Hodge right-hand sides and to

@@ -106,6 +106,7 @@ def _load():
         "lb_fmm_plan_info": [P, P],
         "lb_fmm_plan_arrays": [P, P, P, P, P, P, P, P, P, P],
         "lb_fmm_plan_destroy": [P],
+        "lb_debug_fail_alloc": [P, ctypes.c_int64],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -200,6 +201,11 @@ class Context:
         h = getattr(stream, "cuda_stream", stream)
         self._check(_lib.lb_set_stream(self._h, ctypes.c_void_p(h or 0)))
 
+    def debug_fail_alloc(self, after: int = 0):
+        """Make the device allocation `after` allocations from now fail as out
+        of memory (test hook; after < 0 disarms)."""
+        self._check(_lib.lb_debug_fail_alloc(self._h, int(after)))
+
     def set_profiling(self, on: bool = True):
         self._check(_lib.lb_set_profiling(self._h, 1 if on else 0))
 
@@ -255,7 +261,21 @@ class Context:
         return self._check(_lib.lb_build_corrections(self._h), allow=(LB_EGEOM,))
 
     def load_corrections(self, row_ptr, patch, vals):
+        """Near lists and correction blocks computed elsewhere: row_ptr [N+1]
+        int64, patch [nnzb] int32 (ascending per row), vals [nnzb, 4, n_p]
+        float64.  Host arrays are checked here; the library checks the list
+        structure again on the device (LB_EINVAL on any violation)."""
+        info = self.info()
         nnzb = int(np.asarray(patch).shape[0]) if not hasattr(patch, "shape") else int(patch.shape[0])
+        if tuple(row_ptr.shape) != (info["N"] + 1,) or len(patch.shape) != 1 or \
+                tuple(vals.shape) != (nnzb, NKERNELS, info["np"]):
+            raise ValueError(f"correction arrays must be row_ptr [{info['N'] + 1}], patch [nnzb], "
+                             f"vals [nnzb, {NKERNELS}, {info['np']}]")
+        if all(isinstance(a, np.ndarray) for a in (row_ptr, patch, vals)):
+            try:
+                _checkpoint._check_csr(row_ptr, patch, vals, info["N"], info["npatch"], info["np"])
+            except CheckpointError as e:
+                raise LBError(LB_EINVAL, str(e)) from None
         a = _ptr(row_ptr, np.int64)
         b = _ptr(patch, np.int32)
         c = _ptr(vals, np.float64)

@@ -59,10 +59,28 @@ def load(path, digest: str, near_factor: float, eps_quad: float):
     return row_ptr, patch, vals
 
 
-def _check_csr(row_ptr, patch, vals):
-    if row_ptr.ndim != 1 or row_ptr[0] != 0 or np.any(np.diff(row_ptr) < 0) or row_ptr[-1] != len(patch):
+def _check_csr(row_ptr, patch, vals, N=None, npatch=None, np_=None):
+    """Structure of a correction CSR; N, npatch and np_ (when given) are the
+    surface's node, patch and per-patch node counts."""
+    row_ptr = np.asarray(row_ptr)
+    patch = np.asarray(patch)
+    if row_ptr.ndim != 1 or len(row_ptr) < 2 or row_ptr[0] != 0 or np.any(np.diff(row_ptr) < 0) \
+            or row_ptr[-1] != len(patch):
         raise CheckpointError("row_ptr is not a CSR row pointer for the patch list")
-    if vals.ndim != 3 or vals.shape[0] != len(patch):
-        raise CheckpointError("vals must be [nnzb][kernels][n_p]")
-    if not np.isfinite(vals).all():
-        raise CheckpointError("vals hold non-finite entries")
+    if N is not None and len(row_ptr) != N + 1:
+        raise CheckpointError(f"row_ptr has {len(row_ptr)} entries, the surface needs N + 1 = {N + 1}")
+    if vals is not None:
+        if vals.ndim != 3 or vals.shape[0] != len(patch) or vals.shape[1] != 4 \
+                or (np_ is not None and vals.shape[2] != np_):
+            raise CheckpointError("vals must be [nnzb][4][n_p]")
+        if not np.isfinite(vals).all():
+            raise CheckpointError("vals hold non-finite entries")
+    if len(patch) and (patch.min() < 0 or (npatch is not None and patch.max() >= npatch)):
+        raise CheckpointError("a near patch index lies outside [0, npatch)")
+    # strictly ascending within each row: a step down or a repeat may only
+    # happen where a new row starts
+    if len(patch) > 1:
+        starts = np.zeros(len(patch), dtype=bool)
+        starts[row_ptr[:-1][row_ptr[:-1] < len(patch)]] = True
+        if np.any((np.diff(patch.astype(np.int64)) <= 0) & ~starts[1:]):
+            raise CheckpointError("near patches of a row must be strictly ascending")

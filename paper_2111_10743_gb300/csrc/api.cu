@@ -43,6 +43,8 @@ int lb_ensure(lb_ctx* c, DevBuf& b, size_t bytes) {
   b.p = nullptr;
   b.bytes = 0;
   size_t want = std::max<size_t>(bytes, 256);
+  if (lb_alloc_fails_now(c))
+    return lb_fail(c, LB_ENOMEM, "workspace cudaMalloc(%zu) failed: simulated by lb_debug_fail_alloc", want);
   cudaError_t e = cudaMalloc(&b.p, want);
   if (e != cudaSuccess) {
     b.p = nullptr;
@@ -607,6 +609,28 @@ extern "C" int lb_build_near(lb_ctx* c) {
   return LB_OK;
 }
 
+// Structure check of loaded near lists (bit 0: row_ptr not nondecreasing or
+// outside [0, nnzb]; bit 1: a patch index outside [0, npatch); bit 2: patches
+// of a row not strictly ascending).  Every read stays inside row_ptr [N+1] and
+// patch [nnzb]: a row's patches are read only after its bounds passed.
+__global__ void k_check_csr(int64_t N, int64_t nnzb, int64_t npatch, const int64_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ patch, int* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = row_ptr[i], b = row_ptr[i + 1];
+    if (a < 0 || b < a || b > nnzb) {
+      atomicOr(bad, 1);
+      continue;
+    }
+    int prev = -1;
+    for (int64_t k = a; k < b; ++k) {
+      const int p = patch[k];
+      if (p < 0 || p >= npatch) atomicOr(bad, 2);
+      else if (p <= prev) atomicOr(bad, 4);
+      prev = p;
+    }
+  }
+}
+
 extern "C" int lb_load_corrections(lb_ctx* c, int64_t nnzb, const int64_t* row_ptr, const int32_t* patch,
                                    const double* vals) {
   if (!c) return lb_fail(nullptr, LB_EINVAL, "null context");
@@ -627,13 +651,26 @@ extern "C" int lb_load_corrections(lb_ctx* c, int64_t nnzb, const int64_t* row_p
   LB_CUDA(c, cudaMemcpyAsync(c->near_patch, patch, nnzb * sizeof(int32_t), cudaMemcpyDefault, c->stream));
   LB_CUDA(c, cudaMemcpyAsync(c->vals, vals, nnzb * LB_NKERNELS * c->np * sizeof(double), cudaMemcpyDefault,
                              c->stream));
+  // the first and last row pointer, then the structure of every row, before
+  // any kernel indexes with them
+  LB_CHECK(lb_ensure(c, c->ws_red, 64));
+  int* dbad = (int*)c->ws_red.p;
+  LB_CUDA(c, cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
+  k_check_csr<<<lb_div_up(N, 256) < 1024u ? lb_div_up(N, 256) : 1024u, 256, 0, c->stream>>>(
+      N, nnzb, c->npatch, c->row_ptr, c->near_patch, dbad);
+  LB_LAUNCH(c);
   int64_t ends[2];
+  int bad = 0;
   LB_CUDA(c, cudaMemcpyAsync(&ends[0], c->row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
   LB_CUDA(c, cudaMemcpyAsync(&ends[1], c->row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  LB_CUDA(c, cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   LB_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (ends[0] != 0 || ends[1] != nnzb) {
+  if (ends[0] != 0 || ends[1] != nnzb || bad) {
     free_near(c);
-    return lb_fail(c, LB_EINVAL, "row_ptr must start at 0 and end at nnzb");
+    if (ends[0] != 0 || ends[1] != nnzb) return lb_fail(c, LB_EINVAL, "row_ptr must start at 0 and end at nnzb");
+    if (bad & 1) return lb_fail(c, LB_EINVAL, "row_ptr must be nondecreasing");
+    if (bad & 2) return lb_fail(c, LB_EINVAL, "a near patch index lies outside [0, npatch)");
+    return lb_fail(c, LB_EINVAL, "near patches of a row must be strictly ascending");
   }
   c->nnzb = nnzb;
   c->have_near = c->have_corr = true;
@@ -659,5 +696,11 @@ int lb_require_corr(lb_ctx* c) {
   if (!c) return lb_fail(nullptr, LB_EINVAL, "null context");
   if (!c->have_geom) return lb_fail(c, LB_ESTATE, "no geometry uploaded");
   if (!c->have_corr) return lb_fail(c, LB_ESTATE, "no corrections: call lb_build_corrections or lb_load_corrections");
+  return LB_OK;
+}
+
+extern "C" int lb_debug_fail_alloc(lb_ctx* c, int64_t after) {
+  if (!c) return lb_fail(nullptr, LB_EINVAL, "null context");
+  c->fail_alloc_in = after < 0 ? -1 : after;
   return LB_OK;
 }

@@ -1059,7 +1059,9 @@ __global__ void k_noalloc_pack(int64_t N, int64_t Npad, const double* __restrict
 }
 
 // Address of the scratch array on the current device, looked up once per
-// device (host code cannot use the array's name as a device pointer).
+// device (host code cannot use the array's name as a device pointer).  With
+// CUDA's lazy module loading the array itself is created on a device by this
+// first lookup, so the first call on a device can fail for lack of memory.
 static int noalloc_scratch(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
@@ -1084,10 +1086,12 @@ extern "C" int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, cons
                                    double* out, void* stream) {
   if (npatch < 1 || np < 3 || !X || !nrm || !w || !sigma || !row_ptr || !near_patch || !out)
     return lb_fail(nullptr, LB_EINVAL, "lb_far_sums_noalloc: null pointer, npatch < 1 or np < 3");
+  // compare before multiplying: npatch * np could overflow int64
+  if (np > LB_NOALLOC_MAX_N || npatch > LB_NOALLOC_MAX_N / np)
+    return lb_fail(nullptr, LB_EINVAL,
+                   "lb_far_sums_noalloc: npatch = %lld patches of %d nodes exceeds the maximum of %d nodes",
+                   (long long)npatch, np, LB_NOALLOC_MAX_N);
   const int64_t N = npatch * np;
-  if (N > LB_NOALLOC_MAX_N)
-    return lb_fail(nullptr, LB_EINVAL, "lb_far_sums_noalloc: N = %lld nodes exceeds the maximum of %d",
-                   (long long)N, LB_NOALLOC_MAX_N);
   void* base = nullptr;
   LB_CHECK(noalloc_scratch(&base));
   cudaStream_t st = (cudaStream_t)stream;

@@ -127,6 +127,7 @@ struct lb_ctx {
   double* phi0 = nullptr;           // S[1] for A1's S W S term, in pair precision phi0_prec
   int phi0_prec = -1;
   double* host_pinned = nullptr;  // pinned scalars for GMRES control [LB_PINNED_DOUBLES]
+  int64_t fail_alloc_in = -1;     // lb_debug_fail_alloc: device allocations left before a simulated failure
 };
 
 // ---- error handling --------------------------------------------------------
@@ -162,11 +163,19 @@ struct ProfScope {
 };
 
 // ---- memory ----------------------------------------------------------------
+// True when the allocation about to be made must fail (lb_debug_fail_alloc
+// armed and counted down to it); disarms itself after firing.
+inline bool lb_alloc_fails_now(lb_ctx* c) {
+  if (!c || c->fail_alloc_in < 0) return false;
+  return c->fail_alloc_in-- == 0;
+}
 int lb_ensure(lb_ctx* c, DevBuf& b, size_t bytes);
 template <typename T>
 inline int lb_alloc(lb_ctx* c, T** p, size_t count) {
   if (*p) { cudaFree(*p); *p = nullptr; }
   if (count == 0) return LB_OK;
+  if (lb_alloc_fails_now(c))
+    return lb_fail(c, LB_ENOMEM, "cudaMalloc(%zu) failed: simulated by lb_debug_fail_alloc", count * sizeof(T));
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
   if (e != cudaSuccess) { *p = nullptr; return lb_fail(c, LB_ENOMEM, "cudaMalloc(%zu) failed: %s", count * sizeof(T), cudaGetErrorString(e)); }
   return LB_OK;

@@ -1310,7 +1310,10 @@ extern "C" int lb_harmonic_fields(lb_ctx* c, int nF, const double* F, double* H,
   // per field: rhs (2N), potentials (2N), gradients (6N)
   size_t need = (size_t)(2 * N * nF + 2 * N * nF + 6 * N) * sizeof(double);
   void* mem = nullptr;
-  if (cudaMalloc(&mem, need) != cudaSuccess) return lb_fail(c, LB_ENOMEM, "harmonic-field workspace");
+  if (lb_alloc_fails_now(c) || cudaMalloc(&mem, need) != cudaSuccess) {
+    cudaGetLastError();
+    return lb_fail(c, LB_ENOMEM, "harmonic-field workspace");
+  }
   double* rhs = (double*)mem;                 // [2 nF][N]
   double* pots = rhs + 2 * N * nF;            // [2 nF][N]
   double* grads = pots + 2 * N * nF;          // [2][N][3]
