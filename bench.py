@@ -20,9 +20,16 @@ the 129 MB L2; a barrier and a device synchronise bracket the K steps, and
 the maximum over ranks is reported.  Under torchrun every rank runs its own
 replica of the workload on its own GPU (the solve has no exchange step).
 
---impl reference times the FP64 CPU oracle (tests' reference
-implementation) on the host cores instead: its far-field sums for an A3
-apply (one density, then two) on a bounded sample of target nodes.
+After the timed region the same process times the plain float64 solve of
+the same right-hand side (fp64_plain) and reports the refined solution's
+error against a float64 solve to 1e-12 (err_vs_fp64).  cpu_baseline times
+the FP64 CPU oracle on the host cores: one full A3 apply, one S apply and the
+correction build of sampled rows, from which it estimates the oracle's time
+to solve with and without t_q.
+
+--impl reference times the FP64 CPU oracle (the tests' reference
+implementation) on the host cores instead, one full A3 apply per step.
+--gpus N outside torchrun starts N replicas under torch.distributed.run.
 """
 from __future__ import annotations
 
@@ -250,6 +257,42 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_pairs = info_e["pairs"]
 
+    # the plain float64 form of the same solve on the same GPU, after the
+    # timed region: its time, and the refined solution's error against a
+    # float64 solve to 1e-12
+    fp64_plain = None
+    if args.precision == "fp32_refined" and not args.case.startswith("torus") and not args.no_fp64:
+        u_ref = u.detach().clone()
+        p64 = lb.default_params(eps_quad=1e-12, tol=1e-10, precision=lb.LB_FP64, formulation=lb.LB_A3)
+        ctx.set_params(p64)
+        u64 = torch.empty_like(f)
+        ctx.solve_lb(f, out=u64)                      # warm-up (float64 kernels, workspaces)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1.0)
+        e0.record(stream)
+        _, i64 = ctx.solve_lb(f, out=u64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        p64.tol = 1e-12
+        ctx.set_params(p64)
+        uex = torch.empty_like(f)
+        _, iex = ctx.solve_lb(f, out=uex)
+        torch.cuda.synchronize()
+        ctx.set_params(params)
+        nrm = float(torch.linalg.vector_norm(uex))
+        fp64_plain = {
+            "ms_per_step": round(ms64, 2), "iterations": i64["iterations"],
+            "rel_residual": i64["rel_residual"], "tol": 1e-10,
+            "value": round(i64["pairs"] / (ms64 * 1e-3) / 1e9, 3), "unit": UNIT,
+            "speedup_of_refined": round(ms64 / (ms_max / args.steps), 2),
+            "err_vs_fp64_tol1e-12": {
+                "refined_rel_l2": float(torch.linalg.vector_norm(u_ref - uex)) / nrm,
+                "refined_max_rel": float((u_ref - uex).abs().max() / uex.abs().max()),
+                "fp64_tol1e-10_rel_l2": float(torch.linalg.vector_norm(u64 - uex)) / nrm,
+                "reference_iterations": iex["iterations"], "reference_rel_residual": iex["rel_residual"]},
+        }
+
     # worst rank
     ms_max, e2e_max = worst_over_ranks([ms, sum(e2e_ms) / len(e2e_ms)], device="cuda")
     if rank != 0:
@@ -319,28 +362,42 @@ def run_ours(args):
                 "ms_each": [round(x, 3) for x in e2e_ms],
                 "h2d_bytes_per_step": int(fh.numel() * 8), "d2h_bytes_per_step": int(uh.numel() * 8)},
         "gpu_launches": int(prof["launches"]),
+        **({"fp64_plain": fp64_plain,
+            "err_vs_fp64": fp64_plain["err_vs_fp64_tol1e-12"]["refined_rel_l2"]} if fp64_plain else {}),
         "autotune": {k: v for k, v in ctx.get_tuning().items() if v},
         "clocks": clocks,
     }
     if ws == 1 and not args.no_cpu_baseline and not args.case.startswith("torus"):
-        out["cpu_baseline"] = cpu_baseline(args.cpu_targets)
+        iters64 = fp64_plain["iterations"] if fp64_plain else None
+        out["cpu_baseline"] = cpu_baseline(iters64)
     print(json.dumps(out))
 
 
-def _oracle_step(geo, ptr, pl, rng_seed, targets):
-    from oracle import farsum
-    rng = np.random.default_rng(rng_seed)
-    tau = rng.standard_normal(geo.N)
-    mu = rng.standard_normal((2, geo.N))
-    t0 = time.perf_counter()
-    farsum.far_sums(geo, ptr, pl, tau, targets)       # pass 1: one density
-    farsum.far_sums(geo, ptr, pl, mu, targets)        # pass 2: two densities
-    dt = time.perf_counter() - t0
-    return dt, 3 * len(targets) * geo.N
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def _oracle_setup():
+    """The oracle's geometry and near lists of the benchmark surface, and a
+    Discretisation whose correction blocks have the oracle's CSR structure and
+    seeded values: the timed arithmetic (every far pair, every correction
+    entry) is the oracle's own, and its cost does not depend on the values."""
     from oracle.geometry import build_geometry
+    from oracle.layers import Discretisation
     from workloads.configs import config
     w = config(2)
     s = w.surface
@@ -353,33 +410,78 @@ def _oracle_setup():
         rows += [np.nonzero(r < 2.0 * geo.radius)[0].astype(np.int32) for r in d]
     ptr = np.zeros(N + 1, dtype=np.int64)
     ptr[1:] = np.cumsum([len(r) for r in rows])
-    return geo, ptr, np.concatenate(rows)
+    pl = np.concatenate(rows)
+    vals = np.random.default_rng(8).standard_normal((len(pl), 4, geo.np_)) * 1e-3
+    disc = Discretisation(geo, ptr, pl, vals, 2.0, 1e-12)
+    return w, disc
 
 
-def cpu_baseline(ntargets: int):
-    """The FP64 oracle's far sums on a bounded sample of targets, all host cores."""
-    geo, ptr, pl = _oracle_setup()
-    ntargets = ntargets or geo.N
-    targets = np.random.default_rng(7).choice(geo.N, ntargets, replace=False).astype(np.int64)
-    dt, inter = _oracle_step(geo, ptr, pl, 1, targets)
-    cores = os.cpu_count()
-    return {"value": round(inter / dt / 1e9, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"A3 apply far sums (1 + 2 densities, 4 kernels each) for {ntargets} sampled targets "
-                      f"x {geo.N} sources, FP64 C/OpenMP oracle, {dt:.1f} s"}
+def _oracle_apply(disc, seed):
+    """One A3 apply by the oracle (far sums of 1 + 2 densities over all
+    targets, correction sums, assembly); returns (seconds, far pairs)."""
+    tau = np.random.default_rng(seed).standard_normal(disc.geo.N)
+    t0 = time.perf_counter()
+    disc.apply_A3(tau)
+    return time.perf_counter() - t0, 3 * disc.geo.N * disc.geo.N
+
+
+def _oracle_tq_sample(disc, nrows: int):
+    """Oracle correction build for nrows sampled rows, all host cores;
+    returns (seconds, blocks built)."""
+    from oracle.quadrature import build_corrections
+    g = disc.geo
+    rows = np.random.default_rng(9).choice(g.N, nrows, replace=False)
+    t0 = time.perf_counter()
+    build_corrections(g, disc.near_ptr, disc.near_patch, eps_q=1e-12, rows=rows, workers=os.cpu_count() or 1)
+    dt = time.perf_counter() - t0
+    nblk = int(np.isin(np.repeat(np.arange(g.N), np.diff(disc.near_ptr)), rows).sum())
+    return dt, nblk
+
+
+def cpu_baseline(iters_fp64, tq_rows: int = 32):
+    """The FP64 oracle on all host cores: one full A3 apply (the far sums in
+    C/OpenMP, the correction sums in C/OpenMP, the assembly in numpy), one
+    S apply, and the correction build of sampled rows.  Time to solve is
+    estimated as k applies + 2 S applies (u = S[S[sigma]]), k the iteration
+    count of the float64 GPU solve of the same system (the same operator and
+    GMRES); t_q is the sampled rows' time scaled to every block."""
+    w, disc = _oracle_setup()
+    g = disc.geo
+    t_apply, pairs = _oracle_apply(disc, 1)
+    sig = np.random.default_rng(2).standard_normal(g.N)
+    t0 = time.perf_counter()
+    disc.S(sig)
+    t_s = time.perf_counter() - t0
+    t_smp, nblk = _oracle_tq_sample(disc, tq_rows)
+    t_q = t_smp * len(disc.near_patch) / max(nblk, 1)
+    k = iters_fp64
+    out = {"value": round(pairs / t_apply / 1e9, 4), "unit": UNIT, "cores": os.cpu_count(),
+           "cpu_model": cpu_model(), "kind": "oracle",
+           "sample": (f"one full A3 apply (N = {g.N:,}: far sums of 1 + 2 densities, correction sums, assembly), "
+                      f"one S apply, and the correction build of {tq_rows} sampled rows ({nblk} blocks) "
+                      f"scaled to all {len(disc.near_patch):,} blocks; FP64 C/OpenMP + numpy oracle"),
+           "apply_ms": round(t_apply * 1e3, 1), "s_apply_ms": round(t_s * 1e3, 1),
+           "t_q_s": round(t_q, 1), "t_q_sample_s": round(t_smp, 2)}
+    if k:
+        ts = k * t_apply + 2 * t_s
+        out["time_to_solve_ms"] = round(ts * 1e3, 1)
+        out["time_to_solve_with_t_q_s"] = round(ts + t_q, 1)
+        out["time_to_solve_basis"] = f"{k} applies (the float64 GPU solve's iterations) + 2 S applies"
+    return out
 
 
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
-    geo, ptr, pl = _oracle_setup()
-    args.cpu_targets = args.cpu_targets or geo.N
-    targets = np.random.default_rng(7).choice(geo.N, args.cpu_targets, replace=False).astype(np.int64)
-    for k in range(args.warmup):
-        _oracle_step(geo, ptr, pl, 100 + k, targets[:64])
+    w, disc = _oracle_setup()
+    g = disc.geo
+    for k in range(args.warmup):   # warm-up: the far sums of 64 targets
+        from oracle import farsum
+        farsum.far_sums(g, disc.near_ptr, disc.near_patch, np.ones(g.N), np.arange(64))
     tot, inter = 0.0, 0
     for k in range(args.steps):
-        dt, n = _oracle_step(geo, ptr, pl, k, targets)
+        dt, n = _oracle_apply(disc, 100 + k)
         tot += dt
         inter += n
     value = inter / tot / 1e9
@@ -388,10 +490,12 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot / args.steps * 1e3, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD.format(P=geo.N // 45, N=geo.N), "N": geo.N,
-                   "sample_targets": args.cpu_targets},
-        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"A3 apply far sums for {args.cpu_targets} sampled targets x {geo.N} sources"},
+        "config": {"workload": WORKLOAD.format(P=g.npatch, N=g.N), "N": g.N,
+                   "step": "one full A3 apply by the FP64 oracle (the unit each GMRES iteration repeats)"},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "cpu_model": cpu_model(),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} full A3 applies (far sums of 1 + 2 densities over all "
+                                   f"{g.N:,} targets, correction sums, assembly), FP64 C/OpenMP + numpy"},
         "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -403,8 +507,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32_refined", choices=["fp32_refined", "fp64", "fp32"])
-    ap.add_argument("--cpu-targets", type=int, default=0, help="oracle sample size (0: every target)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 solve after the timed region")
     ap.add_argument("--case", default="full", choices=["full", "small", "torus_batch", "torus_small"],
                     help="full: the benchmark surface; small: 320 patches of the same kind (profiling); "
                          "torus_batch: the torus with 18 right-hand sides solved in lockstep; "
@@ -413,6 +517,15 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: start the replicas under torch.distributed.run
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", str(29500 + os.getpid() % 1000),
+               os.path.abspath(__file__), *sys.argv[1:]]
+        sys.exit(subprocess.call(cmd))
+    if ws != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE {ws}; timing {ws} replica(s)", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -95,3 +95,34 @@ int oracle_far_sums(int64_t N, int64_t np_, const double *X, const double *n,
     return oracle_far_sums_src(N, X, n, near_ptr, near_patch, N / np_, N, np_, X, n, w, nrhs, sigma, ntgt,
                                targets, out);
 }
+
+/* Near-field correction sums (Section 4, the corrected Nystrom form): for
+ * each requested target i, each density r and each kernel k = S, D, S', S''+D'
+ *
+ *   out[r][k][t] = sum_{b in row i} sum_q vals[b][k][q] sigma_r[patch(b) * np + q]
+ *
+ * over the row's blocks b (near_ptr[i] .. near_ptr[i+1]-1), patch(b) =
+ * near_patch[b].  vals is [nnzb][4][np].  A plain loop, parallel over
+ * targets. */
+int oracle_near_apply(int64_t N, int64_t np_, const int64_t *near_ptr, const int32_t *near_patch,
+                      const double *vals, int nrhs, const double *sigma, int64_t ntgt,
+                      const int64_t *targets, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < ntgt; ++t) {
+        const int64_t i = targets[t];
+        for (int r_ = 0; r_ < nrhs; ++r_) {
+            const double *sig = sigma + (int64_t)r_ * N;
+            for (int k = 0; k < 4; ++k) {
+                double acc = 0.0;
+                for (int64_t b = near_ptr[i]; b < near_ptr[i + 1]; ++b) {
+                    const double *v = vals + (b * 4 + k) * np_;
+                    const double *s = sig + (int64_t)near_patch[b] * np_;
+                    for (int64_t q = 0; q < np_; ++q) acc += v[q] * s[q];
+                }
+                out[((int64_t)r_ * 4 + k) * ntgt + t] = acc;
+            }
+        }
+    }
+    return 0;
+}

@@ -1,4 +1,5 @@
-"""Loader for the oracle's C far-sum routine (test infrastructure only).
+"""Loader for the oracle's C far-sum and correction-sum routines (test
+infrastructure only).
 
 Compiles oracle/csrc/farsum.c with gcc (-O2 -fopenmp) into oracle/_build on
 first use, or when the source is newer than the library.
@@ -42,8 +43,31 @@ def _load():
             ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
             ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
             ctypes.c_void_p]
+        lib.oracle_near_apply.restype = ctypes.c_int
+        lib.oracle_near_apply.argtypes = [
+            ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
         _lib = lib
     return _lib
+
+
+def near_sums(geo, near_ptr, near_patch, vals, sigma, targets=None) -> np.ndarray:
+    """Correction sums of all four kernels from the block CSR: [nrhs, 4, ntargets]."""
+    lib = _load()
+    sig = np.ascontiguousarray(np.atleast_2d(sigma), dtype=np.float64)
+    nrhs = sig.shape[0]
+    if targets is None:
+        targets = np.arange(geo.N, dtype=np.int64)
+    targets = np.ascontiguousarray(targets, dtype=np.int64)
+    ptr = np.ascontiguousarray(near_ptr, dtype=np.int64)
+    pl = np.ascontiguousarray(near_patch, dtype=np.int32)
+    v = np.ascontiguousarray(vals, dtype=np.float64)
+    if v.shape != (len(pl), 4, geo.np_) or len(ptr) != geo.N + 1:
+        raise ValueError("correction arrays do not match the geometry")
+    out = np.zeros((nrhs, 4, len(targets)))
+    lib.oracle_near_apply(geo.N, geo.np_, ptr.ctypes.data, pl.ctypes.data, v.ctypes.data, nrhs,
+                          sig.ctypes.data, len(targets), targets.ctypes.data, out.ctypes.data)
+    return out
 
 
 def far_sums(geo, near_ptr, near_patch, sigma, targets=None, far=None) -> np.ndarray:

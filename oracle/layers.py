@@ -41,18 +41,10 @@ class Discretisation:
     far: object = None      # geometry.FarRule: oversampled far-field sources (Section 4), or None
 
     def near_apply(self, sigma: np.ndarray, targets=None) -> np.ndarray:
-        """Correction sums [nrhs, 4, ntargets] from the block CSR."""
-        geo = self.geo
-        sig = np.atleast_2d(sigma).reshape(-1, geo.npatch, geo.np_)
-        if targets is None:
-            targets = np.arange(geo.N)
-        out = np.zeros((sig.shape[0], 4, len(targets)))
-        for t, i in enumerate(targets):
-            for b in range(self.near_ptr[i], self.near_ptr[i + 1]):
-                P = self.near_patch[b]
-                # [4, np] x [nrhs, np] -> [nrhs, 4]
-                out[:, :, t] += sig[:, P, :] @ self.vals[b].T
-        return out
+        """Correction sums [nrhs, 4, ntargets] from the block CSR: for target
+        i, sum over its blocks b of vals[b] (4 x n_p) times the density on
+        patch near_patch[b] (a plain loop in the oracle's C helper)."""
+        return farsum.near_sums(self.geo, self.near_ptr, self.near_patch, self.vals, sigma, targets)
 
     def potentials(self, sigma: np.ndarray, targets=None) -> np.ndarray:
         """All four discretised potentials: [nrhs, 4, ntargets]."""

@@ -280,20 +280,25 @@ def _patch_job(args):
 
 
 def build_corrections(geo: Geometry, near_ptr, near_patch, eps_q: float = 1e-12,
-                      rows=None, m: int = 8, workers: int = 1):
+                      rows=None, m: int = 8, workers: int = 1, blocks=None):
     """Near-field weights as block CSR.
 
     Returns (vals [nnzb, 4, n_p] aligned with near_patch, depth_hits): block b
-    belongs to row i with near_ptr[i] <= b < near_ptr[i+1].  If rows is given,
-    only the blocks of those rows are filled (the rest stay zero).  workers > 1
-    spreads patches over a spawn-started process pool.
+    belongs to row i with near_ptr[i] <= b < near_ptr[i+1].  If rows and/or
+    blocks (a boolean mask over the nnzb blocks) are given, only the blocks of
+    those rows and the selected blocks are filled (the rest stay zero).
+    workers > 1 spreads patches over a spawn-started process pool.
     """
     nnzb = len(near_patch)
     vals = np.zeros((nnzb, 4, geo.np_))
     row_of = np.repeat(np.arange(geo.N), np.diff(near_ptr))
     sel = np.ones(nnzb, dtype=bool)
-    if rows is not None:
-        sel = np.isin(row_of, np.asarray(rows))
+    if rows is not None or blocks is not None:
+        sel = np.zeros(nnzb, dtype=bool)
+        if rows is not None:
+            sel |= np.isin(row_of, np.asarray(rows))
+        if blocks is not None:
+            sel |= np.asarray(blocks, dtype=bool)
     jobs = []
     for P in range(geo.npatch):
         blocks = np.nonzero(sel & (near_patch == P))[0]

@@ -226,40 +226,6 @@ def test_device_pointers_batches_and_errors(lb):
     assert np.all(u == 0.0)
 
 
-def test_full_size_sampled_rows(lb):
-    """Ellipsoid, 1280 patches of order 8 (N = 57,600): the launch shapes of the
-    benchmark, checked on sampled rows that the oracle computes one by one."""
-    from oracle import farsum
-    from oracle.geometry import build_geometry, near_lists
-    from oracle.layers import Discretisation
-    from oracle.quadrature import build_corrections
-    from workloads.configs import config
-    w = config(2)
-    s = w.surface
-    ctx = lb.Context(0, lb.default_params(eps_quad=1e-12))
-    ctx.upload_surface(s)
-    ctx.build_corrections()
-    g = build_geometry(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv)
-    ptr, pl = near_lists(g, 2.0)
-    rp, pa, vals = ctx.get_corrections()
-    assert np.array_equal(rp, ptr) and np.array_equal(pa, pl)
-    rows = np.random.default_rng(29).choice(g.N, 24, replace=False)
-    ov, _ = build_corrections(g, ptr, pl, eps_q=1e-12, rows=rows, workers=WORKERS)
-    sel = np.isin(np.repeat(np.arange(g.N), np.diff(ptr)), rows)
-    assert np.abs(vals[sel] - ov[sel]).max() < 1e-10 * np.abs(ov[sel]).max()
-    sig = np.random.default_rng(30).standard_normal(g.N)
-    ref = farsum.far_sums(g, ptr, pl, sig, targets=rows)[0]
-    # the FP64 oracle sums 57,600 terms of random sign in plain order: its own
-    # rounding is about 1e-11 of the largest sum here, which bounds the DF64 check
-    for prec, tol in ((lb.LB_FP64, 1e-12), (lb.LB_DF64, 2e-11), (lb.LB_FP32, 2e-5)):
-        got = ctx.far_sums(sig, precision=prec)[0][:, rows]
-        for k in range(4):
-            assert _rel(got[k], ref[k]) < tol, (prec, k)
-    disc = Discretisation(g, ptr, pl, np.where(sel[:, None, None], ov, 0.0), 2.0, 1e-12)
-    pot = ctx.apply_S(sig)[0][rows]
-    assert _rel(pot, disc.potentials(sig, targets=rows)[0, 0]) < 1e-10
-
-
 def test_twisted_torus_against_paper_table(lb):
     """Harmonic fields on the twisted torus with the settings of Section 6.3
     (order-9 patches, N = 27,000, eps 5e-8, GMRES 5e-10, A3, float64) against
