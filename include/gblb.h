@@ -186,6 +186,23 @@ int lb_load_corrections(lb_ctx* ctx, int64_t nnzb, const int64_t* row_ptr,
  * the sizes above; vals may be NULL to fetch the lists only). */
 int lb_get_corrections(lb_ctx* ctx, int64_t* row_ptr, int32_t* patch, double* vals);
 
+/* Oversampled far-field rule (Section 4: the smooth far-field quadrature runs
+ * on an oversampled rule; the paper gives no oversampling factor).  uv
+ * [nps][2], w [nps] (host or device) are a node rule of total degree `order`
+ * on T0 (nps = (order+1)(order+2)/2, nodes in T0, weights summing to 1/2).
+ * On every patch the chart X, its tangents X_u, X_v and, in every later pass,
+ * the density are interpolated from the node rule to these nodes (the
+ * Lagrange polynomials of the node rule); the far sums then run over the
+ * npatch * nps interpolated points with normals and area elements of the
+ * interpolated tangents, weights w |X~_u x X~_v|.  Near corrections are
+ * unchanged.  Applies to every single-density pass (lb_far_sums, the
+ * potentials, lb_apply_A, the solves and harmonic fields, which then solve
+ * their right-hand sides one by one); the transposed applies, the adjoint
+ * solve and the node-position gradient return LB_EINVAL while a far rule is
+ * set.  order 0 (uv, w ignored) restores the node rule.  Dropped by
+ * lb_upload_geometry.  Errors: LB_ESTATE (no geometry), LB_EINVAL. */
+int lb_set_far_rule(lb_ctx* ctx, int order, const double* uv, const double* w);
+
 /* Far-field sums alone (Section 4: the target-independent smooth rule over
  * all sources outside Near(i)): out [nrhs][4][N] (host or device) receives
  * sum_{j far} w_j K(x_i, x_j) sigma_j for K = S, D, S', S''+D', computed with

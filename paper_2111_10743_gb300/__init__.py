@@ -107,6 +107,7 @@ def _load():
         "lb_fmm_plan_arrays": [P, P, P, P, P, P, P, P, P, P],
         "lb_fmm_plan_destroy": [P],
         "lb_debug_fail_alloc": [P, ctypes.c_int64],
+        "lb_set_far_rule": [P, ctypes.c_int, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -253,6 +254,16 @@ class Context:
         self._check(_lib.lb_get_geometry(self._h, ctypes.c_void_p(n.ctypes.data), ctypes.c_void_p(w.ctypes.data),
                                          ctypes.c_void_p(H.ctypes.data)))
         return n, w, H
+
+    def set_far_rule(self, order: int = 0, uv=None, w=None):
+        """Oversampled far-field rule (lb_set_far_rule): a node rule of total
+        degree `order` on T0 (uv [nps, 2], w [nps]); order 0 restores the
+        node rule."""
+        if order == 0:
+            self._check(_lib.lb_set_far_rule(self._h, 0, None, None))
+            return
+        a, b = _ptr(uv, np.float64), _ptr(w, np.float64)
+        self._check(_lib.lb_set_far_rule(self._h, int(order), a[0], b[0]))
 
     def build_near(self):
         self._check(_lib.lb_build_near(self._h))

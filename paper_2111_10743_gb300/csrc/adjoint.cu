@@ -498,6 +498,7 @@ int lb_apply_at_op(lb_ctx* c, const double* y, double* out) {
 
 extern "C" int lb_apply_St(lb_ctx* c, int nrhs, const double* y, double* out) {
   LB_CHECK(lb_require_corr(c));
+  if (c->far_order) return lb_fail(c, LB_EINVAL, "transposed applies use the node rule: clear the far rule");
   if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
   LB_CUDA(c, cudaSetDevice(c->device));
   const int64_t N = c->N;
@@ -511,6 +512,7 @@ extern "C" int lb_apply_St(lb_ctx* c, int nrhs, const double* y, double* out) {
 
 extern "C" int lb_apply_At(lb_ctx* c, int nrhs, const double* y, double* out) {
   LB_CHECK(check_adjoint(c));
+  if (c->far_order) return lb_fail(c, LB_EINVAL, "transposed applies use the node rule: clear the far rule");
   if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
   LB_CUDA(c, cudaSetDevice(c->device));
   const int64_t N = c->N;

@@ -236,6 +236,7 @@ static void free_geometry(lb_ctx* c) {
   lb_free(&c->w); lb_free(&c->H); lb_free(&c->ginv); lb_free(&c->J); lb_free(&c->cen);
   lb_free(&c->rad); lb_free(&c->area_p); lb_free(&c->dVinv); lb_free(&c->dDu); lb_free(&c->dDv);
   lb_free(&c->dref); lb_free(&c->pos32); lb_free(&c->nrm32); lb_free(&c->pos64); lb_free(&c->nrm64);
+  lb_free_far_rule(c);
   c->have_geom = false;
 }
 
@@ -266,7 +267,7 @@ extern "C" int lb_destroy(lb_ctx* c) {
   free_near(c);
   for (DevBuf* b : {&c->ws_part, &c->ws_pot, &c->ws_src, &c->ws_vec, &c->ws_red, &c->ws_stage_in,
                     &c->ws_stage_out, &c->ws_gm, &c->ws_quad, &c->ws_bpot, &c->ws_bgm, &c->ws_bvec, &c->ws_dlow, &c->ws_a1,
-                    &c->ws_adj, &c->ws_shape, &c->ws_grad})
+                    &c->ws_adj, &c->ws_shape, &c->ws_grad, &c->ws_fden})
     if (b->p) cudaFree(b->p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -418,20 +418,22 @@ __global__ void k_mask_flags(int64_t N, int np, int tb, int ts, int64_t ntiles, 
   }
 }
 
-int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out) {
+int lb_get_mask_src(lb_ctx* c, int tb, int ts, int snp, int64_t nsrc_pad, MaskTable** out) {
+  const int64_t ntiles = nsrc_pad / ts;
   for (auto& m : c->masks)
-    if (m.tb == tb && m.ts == ts) {
+    if (m.tb == tb && m.ts == ts && m.snp == snp && m.ntiles == ntiles) {
       *out = &m;
       return LB_OK;
     }
   MaskTable m;
   m.tb = tb;
   m.ts = ts;
+  m.snp = snp;
   m.ntb = (c->N + tb - 1) / tb;
-  m.ntiles = c->Npad / ts;
+  m.ntiles = ntiles;
   LB_CHECK(lb_alloc(c, &m.flags, (size_t)(m.ntb * m.ntiles)));
   LB_CUDA(c, cudaMemsetAsync(m.flags, 0, (size_t)(m.ntb * m.ntiles), c->stream));
-  k_mask_flags<<<lb_div_up(c->N, 256), 256, 0, c->stream>>>(c->N, c->np, tb, ts, m.ntiles, c->row_ptr,
+  k_mask_flags<<<lb_div_up(c->N, 256), 256, 0, c->stream>>>(c->N, snp, tb, ts, m.ntiles, c->row_ptr,
                                                               c->near_patch, m.flags);
   LB_LAUNCH(c);
   c->masks.push_back(m);
@@ -439,13 +441,22 @@ int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out) {
   return LB_OK;
 }
 
+int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out) { return lb_get_mask_src(c, tb, ts, c->np, c->Npad, out); }
+
+// Sources of a pass: the nodes themselves, or the oversampled far rule's
+// points (Ns of them, nps per patch) when one is set.
+static inline int64_t src_pad(const lb_ctx* c) { return c->far_order ? c->Nspad : c->Npad; }
+static inline int src_np(const lb_ctx* c) { return c->far_order ? c->nps : c->np; }
+static inline int64_t src_count(const lb_ctx* c) { return c->far_order ? c->Ns : c->N; }
+
 template <typename R, int KIND, int NT, int NTH, int TS>
 static int launch_far_t(lb_ctx* c, const void* srcA, const void* srcB, double* part, int* nsplit_out) {
   typedef typename V4T<R>::type V4;
   const int tb = NT * NTH;
-  if (c->np * 62 < TS) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
+  const int snp = src_np(c);
+  if (snp * 62 < TS) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
   MaskTable* m = nullptr;
-  LB_CHECK(lb_get_mask(c, tb, TS, &m));
+  LB_CHECK(lb_get_mask_src(c, tb, TS, snp, src_pad(c), &m));
   const int64_t ntb = m->ntb, ntiles = m->ntiles;
   // enough CTAs for several per SM: split the source range
   const int64_t want = 6LL * c->sm_count;
@@ -455,11 +466,12 @@ static int launch_far_t(lb_ctx* c, const void* srcA, const void* srcB, double* p
   const V4* tp = sizeof(R) == 4 ? (const V4*)c->pos32 : (const V4*)c->pos64;
   const V4* tn = sizeof(R) == 4 ? (const V4*)c->nrm32 : (const V4*)c->nrm64;
   dim3 grid((unsigned)ntb, (unsigned)nsplit);
-  ProfScope prof(c, (sizeof(R) == 4 ? LB_PROF_FAR32_K1 : LB_PROF_FAR64_K1) + KIND, c->N * c->N);
-  k_far<R, KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, c->np, tp, tn, (const V4*)srcA, (const V4*)srcB,
+  const int64_t pairs = c->N * src_count(c);
+  ProfScope prof(c, (sizeof(R) == 4 ? LB_PROF_FAR32_K1 : LB_PROF_FAR64_K1) + KIND, pairs);
+  k_far<R, KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, snp, tp, tn, (const V4*)srcA, (const V4*)srcB,
                                                           m->flags, ntiles, c->row_ptr, c->near_patch, tps, part);
   LB_LAUNCH(c);
-  lb_pair_counter += c->N * c->N;
+  lb_pair_counter += pairs;
   *nsplit_out = (int)nsplit;
   return LB_OK;
 }
@@ -488,6 +500,14 @@ static int launch_far32x2(lb_ctx* c, const void* srcA, const void* srcB, double*
 
 int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* srcB, double* part, int* nsplit) {
   if (prec == LB_DF64) return lb_far_launch_df(c, kind, srcA, part, nsplit);
+  if (c->far_order && prec != LB_FP64) {  // oversampled sources: the scalar float32 kernels
+    switch (kind) {
+      case FAR_K1: return launch_far_t<float, FAR_K1, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+      case FAR_KALL: return launch_far_t<float, FAR_KALL, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+      case FAR_K2: return launch_far_t<float, FAR_K2, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+      default: return launch_far_t<float, FAR_K4, 4, 128, 128>(c, srcA, srcB, part, nsplit);
+    }
+  }
   if (prec == LB_FP64) {
     switch (kind) {
       case FAR_K1: return launch_far_t<double, FAR_K1, 2, 128, 64>(c, srcA, srcB, part, nsplit);
@@ -526,6 +546,7 @@ __global__ void k_pack(int64_t N, int64_t Npad, const typename V4T<R>::type* __r
 }
 
 static int pack_sources(lb_ctx* c, int prec, const double* d1, const double* d2, void** A, void** B) {
+  if (c->far_order) return lb_far_rule_pack(c, prec, d1, d2, A, B);
   if (prec == LB_DF64) {  // four float4 planes
     LB_CHECK(lb_ensure(c, c->ws_src, 4 * c->Npad * sizeof(float4)));
     *A = c->ws_src.p;
@@ -733,7 +754,7 @@ static int run_epilogue(lb_ctx* c, int prec, int nsplit, int nacc, const double*
 
 static int part_buffer(lb_ctx* c, double** part) {
   // up to 4 accumulators x up to ntiles splits
-  const int64_t max_split = c->Npad / 64;
+  const int64_t max_split = src_pad(c) / 64;
   const int64_t want = std::min<int64_t>(max_split, 6LL * c->sm_count + 8);
   LB_CHECK(lb_ensure(c, c->ws_part, (size_t)(want * 4 * c->N) * sizeof(double)));
   *part = (double*)c->ws_part.p;
@@ -993,7 +1014,7 @@ extern "C" int lb_apply_A(lb_ctx* c, int nrhs, const double* tau, double* out) {
   LB_CHECK(lb_stage_in(c, tau, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&din));
   LB_CHECK(lb_stage_out(c, out, nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dout));
   const int prec = pair_prec(c);
-  if (c->params.formulation == LB_A3 && prec != LB_FP64 && nrhs >= 2) {
+  if (c->params.formulation == LB_A3 && prec != LB_FP64 && nrhs >= 2 && !c->far_order) {
     // several densities per far-field pass
     LB_CHECK(lb_apply_a3_batch(c, prec, nrhs, din, dout, nullptr));
   } else {

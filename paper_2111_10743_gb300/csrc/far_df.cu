@@ -81,9 +81,11 @@ __global__ void __launch_bounds__(NTH) k_far_df(int64_t N, int np, const float4*
                                                 const uint8_t* __restrict__ flags, int64_t ntiles,
                                                 const int64_t* __restrict__ row_ptr,
                                                 const int32_t* __restrict__ near_patch, int tiles_per_split,
-                                                int64_t Npad, double* __restrict__ part) {
+                                                int64_t Npad, const float4* __restrict__ T, int64_t Tpad,
+                                                double* __restrict__ part) {
   constexpr int NO = DfOut<KIND>::n;
-  // S holds four planes of Npad float4: A, B, C, D
+  // S holds four planes of Npad float4: A, B, C, D (sources, np per patch);
+  // T four planes of Tpad float4 in the same layout (targets: the nodes)
   const float4* __restrict__ SA = S;
   const float4* __restrict__ SB = S + Npad;
   const float4* __restrict__ SC = S + 2 * Npad;
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(NTH) k_far_df(int64_t N, int np, const float4*
 #pragma unroll
   for (int j = 0; j < NT; ++j) {
     const int64_t t = t0 + threadIdx.x + j * NTH;
-    const float4 a = SA[t], b = SB[t], c = SC[t], d = SD[t];
+    const float4 a = T[t], b = T[Tpad + t], c = T[2 * Tpad + t], d = T[3 * Tpad + t];
     tv[j][0] = a.x; tv[j][1] = a.y; tv[j][2] = a.z;
     tv[j][3] = b.x; tv[j][4] = b.y; tv[j][5] = b.z;
     tv[j][6] = c.x; tv[j][7] = c.y; tv[j][8] = c.z;
@@ -198,24 +200,40 @@ int lb_pack_df(lb_ctx* c, const double* d1, const double* d2, void* S) {
   return LB_OK;
 }
 
+// the same planes for n explicit points (padded to npad): positions Y, normals
+// nY, weights wY (the oversampled far rule's sources)
+int lb_pack_df_points(lb_ctx* c, int64_t n, int64_t npad, const double* Y, const double* nY, const double* wY,
+                      const double* d1, const double* d2, void* S) {
+  k_pack_df<<<lb_div_up(npad, 256), 256, 0, c->stream>>>(n, npad, Y, nY, wY, d1, d2, c->center[0], c->center[1],
+                                                         c->center[2], c->df_grid, (float4*)S);
+  LB_LAUNCH(c);
+  return LB_OK;
+}
+
 template <int KIND>
 static int launch_df_t(lb_ctx* c, const void* S, double* part, int* nsplit_out) {
   constexpr int NT = 2, NTH = 128, TS = 64;
   const int tb = NT * NTH;
-  if (c->np * 62 < TS) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
+  // sources: the nodes, or the oversampled far rule's points followed by the
+  // nodes' own planes as targets (lb_far_rule_pack)
+  const int snp = c->far_order ? c->nps : c->np;
+  const int64_t spad = c->far_order ? c->Nspad : c->Npad;
+  const float4* T = c->far_order ? (const float4*)S + 4 * spad : (const float4*)S;
+  const int64_t pairs = c->N * (c->far_order ? c->Ns : c->N);
+  if (snp * 62 < TS) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
   MaskTable* m = nullptr;
-  LB_CHECK(lb_get_mask(c, tb, TS, &m));
+  LB_CHECK(lb_get_mask_src(c, tb, TS, snp, spad, &m));
   const int64_t ntb = m->ntb, ntiles = m->ntiles;
   const int64_t want = 6LL * c->sm_count;
   int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(ntiles, (want + ntb - 1) / ntb));
   const int tps = (int)((ntiles + nsplit - 1) / nsplit);
   nsplit = (ntiles + tps - 1) / tps;
   dim3 grid((unsigned)ntb, (unsigned)nsplit);
-  ProfScope prof(c, LB_PROF_FARDF_K1 + KIND, c->N * c->N);
-  k_far_df<KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, c->np, (const float4*)S, m->flags, ntiles,
-                                                           c->row_ptr, c->near_patch, tps, c->Npad, part);
+  ProfScope prof(c, LB_PROF_FARDF_K1 + KIND, pairs);
+  k_far_df<KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, snp, (const float4*)S, m->flags, ntiles,
+                                                           c->row_ptr, c->near_patch, tps, spad, T, c->Npad, part);
   LB_LAUNCH(c);
-  lb_pair_counter += c->N * c->N;
+  lb_pair_counter += pairs;
   *nsplit_out = (int)nsplit;
   return LB_OK;
 }

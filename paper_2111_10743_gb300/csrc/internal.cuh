@@ -34,6 +34,7 @@ enum FarKind {
 // Cached tile-mask table for one (targets per block, sources per tile) shape.
 struct MaskTable {
   int tb = 0, ts = 0;
+  int snp = 0;          // source points per patch the table was built for
   int64_t ntb = 0, ntiles = 0;
   uint8_t* flags = nullptr;  // [ntb][ntiles]: 1 when some pair in the block x tile is near
 };
@@ -128,6 +129,20 @@ struct lb_ctx {
   int phi0_prec = -1;
   double* host_pinned = nullptr;  // pinned scalars for GMRES control [LB_PINNED_DOUBLES]
   int64_t fail_alloc_in = -1;     // lb_debug_fail_alloc: device allocations left before a simulated failure
+
+  // oversampled far rule (lb_set_far_rule): Ns = npatch * nps far-field sources
+  int far_order = 0, nps = 0;
+  int64_t Ns = 0, Nspad = 0;
+  std::vector<double> far_uv, far_w;      // host copy of the far rule on T0
+  double* fI = nullptr;                   // [nps][np] node-rule Lagrange basis at the far-rule nodes
+  double* fY = nullptr;                   // [Ns][3] source positions
+  double* fn = nullptr;                   // [Ns][3] unit normals of the interpolated tangents
+  double* fw = nullptr;                   // [Ns] weights
+  float4* fpos32 = nullptr;               // [Nspad] (y - c, 0), padding far away
+  float4* fnrm32 = nullptr;               // [Nspad]
+  double4_32a* fpos64 = nullptr;          // [Nspad]
+  double4_32a* fnrm64 = nullptr;          // [Nspad]
+  DevBuf ws_fden;                         // upsampled densities / target planes
 };
 
 // ---- error handling --------------------------------------------------------
@@ -221,11 +236,19 @@ int lb_shape_grad_pairs(lb_ctx* c, const double* gu, const double* sg, const dou
                         const double* q1, const double* z, double* grad);
 void lb_free_transpose(lb_ctx* c);
 int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out);
+// the same for sources of snp points per patch padded to nsrc_pad (the
+// oversampled far rule)
+int lb_get_mask_src(lb_ctx* c, int tb, int ts, int snp, int64_t nsrc_pad, MaskTable** out);
+// oversampled far rule: sources for a pass (as pack_sources), and its state
+int lb_far_rule_pack(lb_ctx* c, int prec, const double* d1, const double* d2, void** A, void** B);
+void lb_free_far_rule(lb_ctx* c);
 // float32 hi / lo copies of the correction weights (no-op when present)
 int lb_lowp_vals(lb_ctx* c);
 // hi[i] = (float)x[i], lo[i] = (float)(x[i] - hi[i]) (lo may be null)
 int lb_split_f64(lb_ctx* c, int64_t n, const double* x, float* hi, float* lo);
 int lb_pack_df(lb_ctx* c, const double* d1, const double* d2, void* S);
+int lb_pack_df_points(lb_ctx* c, int64_t n, int64_t npad, const double* Y, const double* nY, const double* wY,
+                      const double* d1, const double* d2, void* S);
 int lb_far_launch_df(lb_ctx* c, int kind, const void* S, double* part, int* nsplit);
 // A3 applied to R densities tau[R][N] -> out[R][N] with several densities per
 // far-field pass (prec LB_FP32 or LB_DF64); u (may be null) receives S[S[tau]]

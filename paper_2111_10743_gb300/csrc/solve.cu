@@ -1006,7 +1006,7 @@ static int solve_batch(lb_ctx* c, int nrhs, const double* f, double* u, lb_solve
     return LB_OK;
   };
   int* dbad = nullptr;
-  if (p.formulation == LB_A3 && p.precision != LB_FP64 && nrhs >= 2) {
+  if (p.formulation == LB_A3 && p.precision != LB_FP64 && nrhs >= 2 && !c->far_order) {
     // several right-hand sides in lockstep, in groups of LB_BATCH_MAX
     lb_solve_info local{};
     if (!info) { local.converged = 1; info = &local; }
@@ -1386,6 +1386,7 @@ __global__ void k_proj_t(int64_t N, const double* __restrict__ z, const double* 
 
 extern "C" int lb_solve_lb_adjoint(lb_ctx* c, int nrhs, const double* gu, double* gf, lb_solve_info* info) {
   LB_CHECK(lb_require_corr(c));
+  if (c->far_order) return lb_fail(c, LB_EINVAL, "the adjoint solve uses the node rule: clear the far rule");
   const bool a2 = c->params.formulation == LB_A2;
   if (c->params.formulation != LB_A3 && !a2)
     return lb_fail(c, LB_EINVAL, "the adjoint solve takes the A3 or A2 formulation");
@@ -1457,6 +1458,7 @@ extern "C" int lb_solve_lb_adjoint(lb_ctx* c, int nrhs, const double* gu, double
 extern "C" int lb_shape_gradient(lb_ctx* c, int nrhs, const double* f, const double* gu, double* grad,
                                  lb_solve_info* info) {
   LB_CHECK(lb_require_corr(c));
+  if (c->far_order) return lb_fail(c, LB_EINVAL, "the node-position gradient uses the node rule: clear the far rule");
   if (c->params.formulation != LB_A3) return lb_fail(c, LB_EINVAL, "the node-position gradient takes the A3 formulation");
   if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
   if (!gu) return lb_fail(c, LB_EINVAL, "null input pointer");

@@ -64,6 +64,17 @@ def ellipsoid():
 
 
 @pytest.fixture(scope="module")
+def ell20():
+    """The ellipsoid (1, 1.5, 2) on the 20 icosahedron faces, order 4 (N = 300),
+    with the sphere's data: curvature varies from node to node."""
+    import dataclasses
+    w = config(1)
+    s = S.ellipsoid((1.0, 1.5, 2.0), 0, 4)
+    return dataclasses.replace(w, surface=s), discretise(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv, eta=2.0,
+                                                         eps_q=1e-12, workers=WORKERS)
+
+
+@pytest.fixture(scope="module")
 def cfg1():
     w = config(1)
     s = w.surface
@@ -490,6 +501,67 @@ def test_planted_missing_SD_gradient_breaks_finite_differences(cfg1, monkeypatch
     monkeypatch.setattr(Sh, "kernel_gradients", planted)
     an = np.sum(Sh.shape_gradient_A3(d, f, u0 - ut) * dX)
     assert abs(fd - an) > 1e-2 * abs(fd)
+
+
+def _tangent_fd(cfg1, drop=None, monkeypatch=None):
+    """Central difference (h = 1e-5) of L = |u - u_t|^2 / 2 along random
+    tangent directions (dX_u, dX_v), the geometry (n, w, H) rebuilt from the
+    perturbed tangents and the correction blocks held fixed; and the oracle's
+    directional derivative <dL/dX_u, dX_u> + <dL/dX_v, dX_v>."""
+    from oracle import shape as Sh
+    from oracle.geometry import build_geometry
+    from oracle.gmres import solve_lb
+    from oracle.layers import Discretisation
+    w_, d = cfg1
+    g = d.geo
+    rng = np.random.default_rng(4)
+    f = w_.f[0] + 0.3 * rng.standard_normal(g.N)
+    ut = rng.standard_normal(g.N)
+
+    def loss(Xu, Xv):
+        gg = build_geometry(g.order, g.basis.uv, g.wref, g.X, Xu, Xv)
+        dd = Discretisation(gg, d.near_ptr, d.near_patch, d.vals, d.eta, d.eps_q)
+        u, *_ = solve_lb(dd, f, "A3", tol=1e-14)
+        return 0.5 * np.sum((u - ut) ** 2), u
+
+    _, u0 = loss(g.Xu, g.Xv)
+    dU = rng.standard_normal((g.N, 3))
+    dV = rng.standard_normal((g.N, 3))
+    h = 1e-5
+    fd = (loss(g.Xu + h * dU, g.Xv + h * dV)[0] - loss(g.Xu - h * dU, g.Xv - h * dV)[0]) / (2 * h)
+    if drop is not None:
+        drop(monkeypatch, Sh)
+    gXu, gXv = Sh.tangent_gradient_A3(d, f, u0 - ut)
+    return fd, np.sum(gXu * dU) + np.sum(gXv * dV)
+
+
+@pytest.mark.parametrize("surf", ["cfg1", "ell20"])
+def test_tangent_gradient_matches_finite_differences(surf, request):
+    """Gradient of L with respect to the chart tangents X_u, X_v, through the
+    normals, weights and mean curvature they define (corrections fixed),
+    against central differences of the oracle's solve: the unit sphere and an
+    ellipsoid (curvature varying over the surface)."""
+    fd, an = _tangent_fd(request.getfixturevalue(surf))
+    assert abs(fd - an) < 1e-7 * abs(fd), (fd, an)
+
+
+@pytest.mark.parametrize("part", ["curvature", "source_normal"])
+def test_planted_tangent_gradient_mistakes(cfg1, monkeypatch, part):
+    """Dropping the curvature term, or the S''+D' source-normal term, moves the
+    tangent gradient's directional derivative outside the difference pin."""
+    def drop(mp, Sh):
+        if part == "curvature":
+            orig = Sh._tangent_chain
+            mp.setattr(Sh, "_tangent_chain", lambda g, gn, gw, gH: orig(g, gn, gw, 0.0 * gH))
+        else:
+            orig = Sh._far_kernels
+
+            def planted(disc):
+                KS, KSp, KSD, dSp, dSDx, dSDy = orig(disc)
+                return KS, KSp, KSD, dSp, dSDx, 0.0 * dSDy
+            mp.setattr(Sh, "_far_kernels", planted)
+    fd, an = _tangent_fd(cfg1, drop, monkeypatch)
+    assert abs(fd - an) > 1e-4 * abs(fd), (fd, an)
 
 
 # --- near weights on flat patches against closed forms ------------------------
