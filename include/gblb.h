@@ -328,6 +328,25 @@ int lb_solve_lb_adjoint(lb_ctx* ctx, int nrhs, const double* gu, double* gf, lb_
 int lb_shape_gradient(lb_ctx* ctx, int nrhs, const double* f, const double* gu, double* grad,
                       lb_solve_info* info);
 
+/* Gradients of a loss of the A3 solve with respect to the surface inputs of
+ * lb_upload_geometry (not in the paper): node positions X and chart tangents
+ * X_u, X_v, taken as independent inputs, with the correction blocks and the
+ * near lists held fixed (they are built once from the geometry and reused).
+ *   gX: as lb_shape_gradient (X enters through the far pair sums);
+ *   gXu, gXv: X_u and X_v enter through the unit normals
+ *     n = X_u x X_v / |X_u x X_v| (target normal of S' and S''+D', source
+ *     normal of S''+D'), the weights w = w_ref |X_u x X_v| (every far sum, the
+ *     mean W of A3 and the projection P f = f - W f) and the mean curvature
+ *     H = -1/2 tr(g^-1 L) with L_ab = X_ab . n and X_uu = D_u X_u,
+ *     X_vv = D_v X_v, X_uv = (D_v X_u + D_u X_v)/2 (Sections 2, 4.3).
+ * Shares the two float64 GMRES solves (A3 and A3^T) between the outputs.
+ * f, g_u [nrhs][N]; gX, gXu, gXv [nrhs][N][3]: host or device, any output may
+ * be NULL (gXu and gXv together).  LB_EINVAL unless the formulation is LB_A3,
+ * while a far rule is set, or with no output; info as for lb_solve_lb;
+ * LB_ENOTCONVERGED when a GMRES does not reach tol. */
+int lb_geometry_gradient(lb_ctx* ctx, int nrhs, const double* f, const double* gu, double* gX, double* gXu,
+                         double* gXv, lb_solve_info* info);
+
 /* Launch shapes chosen by the batched passes' tuner (not part of the paper;
  * several-density passes time each shape once per process and surface and
  * keep the fastest): shapes[8], indexed by precision (0 float32, 1

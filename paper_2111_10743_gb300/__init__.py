@@ -108,6 +108,7 @@ def _load():
         "lb_fmm_plan_destroy": [P],
         "lb_debug_fail_alloc": [P, ctypes.c_int64],
         "lb_set_far_rule": [P, ctypes.c_int, P, P],
+        "lb_geometry_gradient": [P, ctypes.c_int, P, P, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -238,6 +239,23 @@ class Context:
         self.N = self.info()["N"]
         host = [a.detach().cpu().numpy() if hasattr(a, "detach") else a for a in (ref_uv, ref_w, X, Xu, Xv)]
         self._digest = _checkpoint.geometry_digest(npatch, order, *host)
+        # host copies of the uploaded surface, for check_geometry
+        self._geom_host = {k: np.array(v, dtype=np.float64).reshape(-1, 3)
+                           for k, v in zip(("X", "Xu", "Xv"), host[2:])}
+
+    def check_geometry(self, **arrays):
+        """Raise ValueError unless every given array (X=, Xu=, Xv=; numpy or
+        torch, host or device) equals the uploaded one exactly."""
+        if getattr(self, "_geom_host", None) is None:
+            raise LBError(LB_ESTATE, "no geometry uploaded")
+        for k, a in arrays.items():
+            if a is None:
+                continue
+            h = a.detach().cpu().numpy() if hasattr(a, "detach") else np.asarray(a)
+            ref = self._geom_host[k]
+            if h.size != ref.size or not np.array_equal(h.reshape(-1, 3), ref):
+                raise ValueError(f"{k} differs from the uploaded surface: upload it (and rebuild or load the "
+                                 f"corrections) before solving")
 
     def upload_surface(self, surf):
         """Convenience: upload a workloads.surfaces.Surface-like object."""
@@ -413,6 +431,30 @@ class Context:
                     allow=(LB_ENOTCONVERGED,) if allow_unconverged else ())
         return res, info.as_dict()
 
+    def geometry_gradient(self, f, gu, want_x=True, want_tangents=True, out=None, allow_unconverged=False):
+        """Gradients [nrhs, N, 3] of a loss of the A3 solve with respect to
+        the node positions X and the chart tangents X_u, X_v (corrections and
+        near lists held fixed), given g_u = dL/du.  Returns (gX or None, gXu
+        or None, gXv or None, info); out = (gX, gXu, gXv) buffers, optional."""
+        nrhs = self._nrhs(f)
+        if self._nrhs(gu) != nrhs:
+            raise ValueError("f and gu need the same number of right-hand sides")
+        p, keep = _ptr(f, np.float64)
+        q, keep2 = _ptr(gu, np.float64)
+        outs = out if out is not None else (None, None, None)
+        ptrs, res = [], []
+        for want, o in zip((want_x, want_tangents, want_tangents), outs):
+            if want:
+                pp, rr = _out(o, np.float64, (nrhs, self.N, 3))
+            else:
+                pp, rr = None, None
+            ptrs.append(pp)
+            res.append(rr)
+        info = lb_solve_info()
+        self._check(_lib.lb_geometry_gradient(self._h, nrhs, p, q, *ptrs, ctypes.byref(info)),
+                    allow=(LB_ENOTCONVERGED,) if allow_unconverged else ())
+        return res[0], res[1], res[2], info.as_dict()
+
     def harmonic_fields(self, F, out=None):
         nF = self._nrhs(F, 3)
         p, keep = _ptr(F, np.float64)
@@ -481,37 +523,44 @@ def _torch_fns():
             return gf, None
 
     class SolveLBShape(torch.autograd.Function):
-        """u = solve_lb(f) differentiable in f and in the node positions X.
+        """u = solve_lb(f) differentiable in f and in the surface inputs X,
+        X_u, X_v of the upload (each may be None: not differentiated).
 
-        X: float64 tensor [N, 3] holding the positions uploaded to ctx_lb
-        (it stands for them; the solve reads the context's copy).  Its
-        gradient is the library's node-position gradient with the
-        corrections, w, n and H held fixed, summed over the right-hand
-        sides; A3 only."""
+        The given arrays must equal the uploaded ones (checked; ValueError
+        otherwise).  Their gradients are the library's geometry gradients
+        (A3; correction blocks and near lists held fixed), summed over the
+        right-hand sides."""
 
         @staticmethod
-        def forward(ctx, f, X, ctx_lb):
+        def forward(ctx, f, X, Xu, Xv, ctx_lb):
+            ctx_lb.check_geometry(X=X, Xu=Xu, Xv=Xv)
             u = torch.empty_like(f)
             fd = f.detach().contiguous()
             ctx_lb.solve_lb(fd, out=u)
             ctx.ctx_lb = ctx_lb
             ctx.save_for_backward(fd)
-            ctx.x_shape = X.shape
+            ctx.shapes = tuple(None if a is None else a.shape for a in (X, Xu, Xv))
             return u
 
         @staticmethod
         def backward(ctx, gu):
             (f,) = ctx.saved_tensors
             gu = gu.contiguous()
-            gf = gX = None
+            gf = None
             if ctx.needs_input_grad[0]:
                 gf = torch.empty_like(gu)
                 ctx.ctx_lb.solve_lb_adjoint(gu, out=gf)
-            if ctx.needs_input_grad[1]:
-                g = torch.empty(gu.shape + (3,), dtype=gu.dtype, device=gu.device)
-                ctx.ctx_lb.shape_gradient(f, gu, out=g)
-                gX = g.sum(dim=0).reshape(ctx.x_shape)
-            return gf, gX, None
+            want_x = ctx.needs_input_grad[1]
+            want_t = ctx.needs_input_grad[2] or ctx.needs_input_grad[3]
+            grads = [None, None, None]
+            if want_x or want_t:
+                bufs = tuple(torch.empty(gu.shape + (3,), dtype=gu.dtype, device=gu.device) if w else None
+                             for w in (want_x, want_t, want_t))
+                ctx.ctx_lb.geometry_gradient(f, gu, want_x, want_t, out=bufs)
+                for k in range(3):
+                    if ctx.needs_input_grad[1 + k]:
+                        grads[k] = bufs[k].sum(dim=0).reshape(ctx.shapes[k])
+            return (gf, *grads, None)
 
     class ApplyA(torch.autograd.Function):
         """y = A tau with gradient A^T g_y."""
@@ -532,14 +581,15 @@ def _torch_fns():
     return SolveLB, ApplyA, SolveLBShape
 
 
-def solve_lb_autograd(f, ctx_lb, X=None):
+def solve_lb_autograd(f, ctx_lb, X=None, Xu=None, Xv=None):
     """Differentiable mean-zero Laplace-Beltrami solve (A3 or A2): u = solve(f).
 
-    With X (a tensor [N, 3] standing for the uploaded node positions) the
-    solve is also differentiable in X (A3; corrections held fixed)."""
-    if X is None:
+    With X, Xu or Xv (tensors [N, 3] equal to the uploaded node positions and
+    chart tangents; checked) the solve is also differentiable in them (A3;
+    correction blocks and near lists held fixed)."""
+    if X is None and Xu is None and Xv is None:
         return _torch_fns()[0].apply(f, ctx_lb)
-    return _torch_fns()[2].apply(f, X, ctx_lb)
+    return _torch_fns()[2].apply(f, X, Xu, Xv, ctx_lb)
 
 
 def apply_A_autograd(tau, ctx_lb):

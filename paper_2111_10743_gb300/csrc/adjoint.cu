@@ -834,3 +834,412 @@ int lb_shape_grad_pairs(lb_ctx* c, const double* gu, const double* sg, const dou
   LB_LAUNCH(c);
   return LB_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Gradient with respect to the chart tangents X_u, X_v (not in the paper).
+// Input model: X, X_u, X_v are the upload's independent inputs; the
+// correction blocks and the near lists are held fixed.  X_u, X_v enter A3
+// through the unit normals n = X_u x X_v / |X_u x X_v| (target normal of S'
+// and S''+D', source normal of S''+D'), the weights w = w_ref |X_u x X_v|
+// (every far sum, the mean W, the projection P f = f - W f) and the mean
+// curvature H = -1/2 tr(g^-1 L), L_ab = X_ab . n, X_uu = D_u X_u,
+// X_vv = D_v X_v, X_uv = (D_v X_u + D_u X_v)/2 (Section 2).  With the six
+// bilinear terms a_m . K_m b_m of the node-position gradient (same a_m, b_m):
+//   dL/dw_j = sum_m b_m,j U_m,j - eta_z [(S mu2)_j - W S mu2 + (P f)_j],
+//     U_m,j = sum_{i far} a_m,i K_m(x_i, x_j),  eta_z = sum z / |Gamma|;
+//   dL/dn_i = a_2,i V1_i + a_3,i V2_i + a_4,i V3_i + z_i V4_i,
+//     V1, V2, V3 = sum_{j far} w_j (mu1, sigma, mu2)_j dS'/dn_x,
+//     V4 = sum_{j far} w_j mu2_j d(S''+D')/dn_x;
+//   dL/dn_j += w_j mu2_j sum_{i far} z_i d(S''+D')/dn_y;
+//   dL/dH_i = 2 z_i (S' mu2)_i;
+// then the chain rule through n, |X_u x X_v| and H.  With a = n_x.d,
+// e = n_x - n_y, b = e.d (d = x_i - x_j, 1/(4 pi) applied at the end):
+//   dS'/dn_x = -d / r^3,
+//   d(S''+D')/dn_x = [3 (a + b) d / r^2 - e] / r^3,
+//   d(S''+D')/dn_y = [-3 a d / r^2 + e] / r^3.
+#define TG_NF 12  // forward: V1 .. V4, three components each
+#define TG_NT 9   // transposed: U_0 .. U_5, then the source-normal vector
+
+// forward sums: Q [Npad][3] = w (sigma, mu1, mu2); part [split][12][N]
+__global__ void __launch_bounds__(GR_NTH) k_tan_fwd(int64_t N, int np, const double4_32a* __restrict__ pos,
+                                                    const double4_32a* __restrict__ nrm, const double* __restrict__ Q,
+                                                    const uint8_t* __restrict__ flags, int64_t ntiles,
+                                                    const int64_t* __restrict__ row_ptr,
+                                                    const int32_t* __restrict__ near_patch, int tiles_per_split,
+                                                    double* __restrict__ part) {
+  __shared__ double4_32a sP[TT_TS], sN[TT_TS];
+  __shared__ double sQ[TT_TS][3];
+  __shared__ int sLp[TT_TS];
+  const int64_t t = (int64_t)blockIdx.x * GR_NTH + threadIdx.x;  // < Npad
+  const double4_32a p = pos[t], n = nrm[t];
+  const double xi[3] = {p.x, p.y, p.z}, ni[3] = {n.x, n.y, n.z};
+  double acc[TG_NF];
+#pragma unroll
+  for (int o = 0; o < TG_NF; ++o) acc[o] = 0.0;
+  const int64_t tile_b = (int64_t)blockIdx.y * tiles_per_split;
+  const int64_t tile_e = min(ntiles, tile_b + tiles_per_split);
+  for (int64_t tile = tile_b; tile < tile_e; ++tile) {
+    const int64_t s0 = tile * TT_TS;
+    const int64_t P0 = s0 / np;
+    for (int s = threadIdx.x; s < TT_TS; s += GR_NTH) {
+      sP[s] = pos[s0 + s];
+      sN[s] = nrm[s0 + s];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sQ[s][k] = Q[(s0 + s) * 3 + k];
+      sLp[s] = (int)((s0 + s) / np - P0);
+    }
+    __syncthreads();
+    unsigned long long m = 0ull;
+    if (flags[(int64_t)blockIdx.x * ntiles + tile] != 0 && t < N)
+      for (int64_t bb = row_ptr[t]; bb < row_ptr[t + 1]; ++bb) {
+        const int64_t dd = (int64_t)near_patch[bb] - P0;
+        if (dd >= 0 && dd < 64) m |= 1ull << dd;
+      }
+    for (int s = 0; s < TT_TS; ++s) {
+      const double4_32a a4 = sP[s], b4 = sN[s];
+      const double d[3] = {xi[0] - a4.x, xi[1] - a4.y, xi[2] - a4.z};
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      const bool masked = ((m >> sLp[s]) & 1ull) || t >= N;
+      const double rinv = masked ? 0.0 : rsqrt(r2);
+      const double rinv2 = rinv * rinv, rinv3 = rinv2 * rinv;
+      const double e[3] = {ni[0] - b4.x, ni[1] - b4.y, ni[2] - b4.z};
+      const double a = ni[0] * d[0] + ni[1] * d[1] + ni[2] * d[2];
+      const double b = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
+      const double cd = 3.0 * (a + b) * rinv2 * rinv3;
+      const double qs = sQ[s][0], q1 = sQ[s][1], q2 = sQ[s][2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double gp = -d[k] * rinv3;                     // dS'/dn_x
+        const double gx = cd * d[k] - e[k] * rinv3;          // d(S''+D')/dn_x
+        acc[k] += q1 * gp;
+        acc[3 + k] += qs * gp;
+        acc[6 + k] += q2 * gp;
+        acc[9 + k] += q2 * gx;
+      }
+    }
+    __syncthreads();
+  }
+  if (t >= N) return;
+#pragma unroll
+  for (int o = 0; o < TG_NF; ++o) part[((int64_t)blockIdx.y * TG_NF + o) * N + t] = acc[o];
+}
+
+// transposed sums: outputs j, sources i with patch(j) not in Near(i).
+// A [Npad][6] = (a0 .. a5) at the sources; part [split][9][N]
+__global__ void __launch_bounds__(GR_NTH) k_tan_tr(int64_t N, int np, const double4_32a* __restrict__ pos,
+                                                   const double4_32a* __restrict__ nrm, const double* __restrict__ A,
+                                                   const uint8_t* __restrict__ tflag,
+                                                   const unsigned long long* __restrict__ tmask, int64_t ntiles,
+                                                   int tiles_per_split, double* __restrict__ part) {
+  __shared__ double4_32a sP[TT_TS], sN[TT_TS];
+  __shared__ double sA[TT_TS][6];
+  const int64_t t = (int64_t)blockIdx.x * GR_NTH + threadIdx.x;  // < Npad
+  const double4_32a p = pos[t], n = nrm[t];
+  const double xj[3] = {p.x, p.y, p.z}, nj[3] = {n.x, n.y, n.z};
+  const int64_t pj = t < N ? t / np : -1;
+  double acc[TG_NT];
+#pragma unroll
+  for (int o = 0; o < TG_NT; ++o) acc[o] = 0.0;
+  const int64_t tile_b = (int64_t)blockIdx.y * tiles_per_split;
+  const int64_t tile_e = min(ntiles, tile_b + tiles_per_split);
+  for (int64_t tile = tile_b; tile < tile_e; ++tile) {
+    const int64_t s0 = tile * TT_TS;
+    for (int s = threadIdx.x; s < TT_TS; s += GR_NTH) {
+      sP[s] = pos[s0 + s];
+      sN[s] = nrm[s0 + s];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sA[s][k] = A[(s0 + s) * 6 + k];
+    }
+    __syncthreads();
+    const bool any = tflag[((int64_t)blockIdx.x * GR_NTH / TT_TB) * ntiles + tile] != 0;
+    const unsigned long long m = (any && pj >= 0) ? tmask[pj * ntiles + tile] : 0ull;
+    for (int s = 0; s < TT_TS; ++s) {
+      const double4_32a a4 = sP[s], b4 = sN[s];
+      const double d[3] = {a4.x - xj[0], a4.y - xj[1], a4.z - xj[2]};  // x_i - x_j
+      const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      const bool masked = ((m >> s) & 1ull) || pj < 0;
+      const double rinv = masked ? 0.0 : rsqrt(r2);
+      const double rinv2 = rinv * rinv, rinv3 = rinv2 * rinv;
+      const double ni[3] = {b4.x, b4.y, b4.z};
+      const double e[3] = {ni[0] - nj[0], ni[1] - nj[1], ni[2] - nj[2]};
+      const double a = ni[0] * d[0] + ni[1] * d[1] + ni[2] * d[2];
+      const double b = e[0] * d[0] + e[1] * d[1] + e[2] * d[2];
+      const double e2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+      const double kS = rinv, kSp = -a * rinv3, kSD = (3.0 * a * b * rinv2 - 0.5 * e2) * rinv3;
+      acc[0] += sA[s][0] * kS;
+      acc[1] += sA[s][1] * kS;
+      acc[2] += sA[s][2] * kSp;
+      acc[3] += sA[s][3] * kSp;
+      acc[4] += sA[s][4] * kSp;
+      acc[5] += sA[s][5] * kSD;
+      const double ca = -3.0 * a * rinv2 * rinv3 * sA[s][5];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc[6 + k] += ca * d[k] + sA[s][5] * e[k] * rinv3;  // d(S''+D')/dn_y
+    }
+    __syncthreads();
+  }
+  if (t >= N) return;
+#pragma unroll
+  for (int o = 0; o < TG_NT; ++o) part[((int64_t)blockIdx.y * TG_NT + o) * N + t] = acc[o];
+}
+
+// out[o][j] = 1/(4 pi) sum_s part[s][o][j]
+__global__ void k_reduce_tg(int64_t N, int nsplit, int nout, const double* __restrict__ part,
+                            double* __restrict__ out) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  for (int o = 0; o < nout; ++o) {
+    double s = 0;
+    for (int k = 0; k < nsplit; ++k) s += part[((int64_t)k * nout + o) * N + j];
+    out[(int64_t)o * N + j] = s * LB_INV4PI;
+  }
+}
+
+struct TanIn {
+  const double *a[6], *b[6];   // the bilinear terms
+  const double* V;             // [12][N] forward sums
+  const double* U;             // [9][N] transposed sums
+  const double* z;             // adjoint solution
+  const double* mu2;
+  const double* Smu2;          // S mu2 (far + near)
+  const double* Spmu2;         // S' mu2 (far + near)
+  const double* pf;            // P f
+  const double* partial;       // [3][nblk] partial sums: z, w S mu2 (the weighted mean)
+  int npart;
+};
+
+// per node: dL/dn, dL/dw, dL/dH -> the local parts of dL/dX_u, dL/dX_v and
+// the vectors gXuu, gXvv, gXuv that the patch differentiation distributes
+__global__ void k_tan_local(int64_t N, int np, TanIn in, const double* __restrict__ Xu, const double* __restrict__ Xv,
+                            const double* __restrict__ nrm, const double* __restrict__ w,
+                            const double* __restrict__ Jn, const double* __restrict__ ginv,
+                            const double* __restrict__ ref, const double* __restrict__ Du,
+                            const double* __restrict__ Dv, double area, double* __restrict__ gXu,
+                            double* __restrict__ gXv, double* __restrict__ g2) {
+  __shared__ double eta_z, eta;
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int k = 0; k < in.npart; ++k) {
+      s0 += in.partial[k];
+      s1 += in.partial[in.npart + k];
+    }
+    eta_z = s0 / area;
+    eta = s1 / area;
+  }
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t P = i / np;
+  const int q = (int)(i - P * np);
+  // weights
+  double gw = -eta_z * (in.Smu2[i] - eta + in.pf[i]);
+#pragma unroll
+  for (int m = 0; m < 6; ++m) gw += in.b[m][i] * in.U[(int64_t)m * N + i];
+  // normals
+  double gn[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    gn[k] = in.a[2][i] * in.V[(int64_t)k * N + i] + in.a[3][i] * in.V[(int64_t)(3 + k) * N + i] +
+            in.a[4][i] * in.V[(int64_t)(6 + k) * N + i] + in.z[i] * in.V[(int64_t)(9 + k) * N + i] +
+            w[i] * in.mu2[i] * in.U[(int64_t)(6 + k) * N + i];
+  // curvature
+  const double gH = 2.0 * in.z[i] * in.Spmu2[i];
+  const double* xu = Xu + 3 * i;
+  const double* xv = Xv + 3 * i;
+  const double n[3] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+  double xuu[3] = {0, 0, 0}, xvv[3] = {0, 0, 0}, xuv[3] = {0, 0, 0};
+  for (int bq = 0; bq < np; ++bq) {
+    const double du = Du[q * np + bq], dv = Dv[q * np + bq];
+    const double* pu = Xu + 3 * (P * np + bq);
+    const double* pv = Xv + 3 * (P * np + bq);
+    for (int k = 0; k < 3; ++k) {
+      xuu[k] += du * pu[k];
+      xvv[k] += dv * pv[k];
+      xuv[k] += 0.5 * (dv * pu[k] + du * pv[k]);
+    }
+  }
+  const double G11 = ginv[3 * i], G12 = ginv[3 * i + 1], G22 = ginv[3 * i + 2];
+  const double L11 = xuu[0] * n[0] + xuu[1] * n[1] + xuu[2] * n[2];
+  const double L12 = xuv[0] * n[0] + xuv[1] * n[1] + xuv[2] * n[2];
+  const double L22 = xvv[0] * n[0] + xvv[1] * n[1] + xvv[2] * n[2];
+  // M = 1/2 G L G (symmetric)
+  const double GL11 = G11 * L11 + G12 * L12, GL12 = G11 * L12 + G12 * L22;
+  const double GL21 = G12 * L11 + G22 * L12, GL22 = G12 * L12 + G22 * L22;
+  const double M11 = 0.5 * (GL11 * G11 + GL12 * G12);
+  const double M12 = 0.5 * (GL11 * G12 + GL12 * G22);
+  const double M22 = 0.5 * (GL21 * G12 + GL22 * G22);
+  double gu_[3], gv_[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gn[k] += -0.5 * gH * (G11 * xuu[k] + 2.0 * G12 * xuv[k] + G22 * xvv[k]);
+    g2[(int64_t)k * N + i] = -0.5 * gH * G11 * n[k];        // dL/dX_uu
+    g2[(int64_t)(3 + k) * N + i] = -0.5 * gH * G22 * n[k];  // dL/dX_vv
+    g2[(int64_t)(6 + k) * N + i] = -gH * G12 * n[k];        // dL/dX_uv
+    gu_[k] = gH * (2.0 * M11 * xu[k] + 2.0 * M12 * xv[k]);
+    gv_[k] = gH * (2.0 * M22 * xv[k] + 2.0 * M12 * xu[k]);
+  }
+  // n = c / |c|, w = w_ref |c|, c = X_u x X_v
+  const double gJ = ref[3 * q + 2] * gw;
+  const double ng = n[0] * gn[0] + n[1] * gn[1] + n[2] * gn[2];
+  const double iJ = 1.0 / Jn[i];
+  double gc[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) gc[k] = (gn[k] - ng * n[k]) * iJ + gJ * n[k];
+  gu_[0] += xv[1] * gc[2] - xv[2] * gc[1];
+  gu_[1] += xv[2] * gc[0] - xv[0] * gc[2];
+  gu_[2] += xv[0] * gc[1] - xv[1] * gc[0];
+  gv_[0] += gc[1] * xu[2] - gc[2] * xu[1];
+  gv_[1] += gc[2] * xu[0] - gc[0] * xu[2];
+  gv_[2] += gc[0] * xu[1] - gc[1] * xu[0];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gXu[3 * i + k] = gu_[k];
+    gXv[3 * i + k] = gv_[k];
+  }
+}
+
+// patch differentiation transposed: gX_u[P,q] += sum_i Du[i][q] gXuu[P,i] + 1/2 Dv[i][q] gXuv[P,i],
+// gX_v[P,q] += sum_i Dv[i][q] gXvv[P,i] + 1/2 Du[i][q] gXuv[P,i]
+__global__ void k_tan_diff(int64_t N, int np, const double* __restrict__ Du, const double* __restrict__ Dv,
+                           const double* __restrict__ g2, double* __restrict__ gXu, double* __restrict__ gXv) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const int64_t P = j / np;
+  const int q = (int)(j - P * np);
+  double su[3] = {0, 0, 0}, sv[3] = {0, 0, 0};
+  for (int ii = 0; ii < np; ++ii) {
+    const int64_t i = P * np + ii;
+    const double du = Du[ii * np + q], dv = Dv[ii * np + q];
+    for (int k = 0; k < 3; ++k) {
+      const double uu = g2[(int64_t)k * N + i], vv = g2[(int64_t)(3 + k) * N + i], uv = g2[(int64_t)(6 + k) * N + i];
+      su[k] += du * uu + 0.5 * dv * uv;
+      sv[k] += dv * vv + 0.5 * du * uv;
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    gXu[3 * j + k] += su[k];
+    gXv[3 * j + k] += sv[k];
+  }
+}
+
+// partials of sum z (first row) and sum w S mu2 (second row)
+__global__ void k_tan_sums(int64_t N, const double* __restrict__ z, const double* __restrict__ w,
+                           const double* __restrict__ s, double* __restrict__ partial) {
+  __shared__ double sh[2][256];
+  double a = 0, b = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    a += z[i];
+    b += w[i] * s[i];
+  }
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + k];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = sh[0][0];
+    partial[gridDim.x + blockIdx.x] = sh[1][0];
+  }
+}
+
+int lb_tangent_grad_pairs(lb_ctx* c, const double* gu, const double* pf, const double* sg, const double* mu1,
+                          const double* mu2, const double* q1, const double* z, double* gXu, double* gXv) {
+  LB_CHECK(lb_build_transpose(c));
+  LB_CHECK(ensure_v1(c));
+  const int64_t N = c->N, Npad = c->Npad;
+  MaskTable* mt = nullptr;
+  LB_CHECK(lb_get_mask(c, GR_NTH, TT_TS, &mt));
+  const int64_t ntb = (N + GR_NTH - 1) / GR_NTH, ntiles = Npad / TT_TS;
+  if (mt->ntb != ntb || mt->ntiles != ntiles || c->t_ntiles != ntiles)
+    return lb_fail(c, LB_EINVAL, "gradient tile tables disagree");
+  const int64_t want = 6LL * c->sm_count;
+  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>({ntiles, (want + ntb - 1) / ntb, (int64_t)32}));
+  const int tps = (int)((ntiles + nsplit - 1) / nsplit);
+  nsplit = (ntiles + tps - 1) / tps;
+  // vectors: h2z, tp [3], a0..a3 [4], V [12], U [9], pot2 [4], g2 [9], partial [2 T_RB];
+  // scratch: packed [Npad][6], part [nsplit][12][N]
+  const size_t nvec = (size_t)(1 + 3 + 4 + TG_NF + TG_NT + 4 + 9) * N + 2 * T_RB;
+  LB_CHECK(lb_ensure(c, c->ws_grad, (nvec + (size_t)Npad * 6 + (size_t)nsplit * TG_NF * N) * sizeof(double)));
+  double* h2z = (double*)c->ws_grad.p;
+  double* tp = h2z + N;
+  double* av = tp + 3 * N;
+  double* V = av + 4 * N;
+  double* U = V + TG_NF * N;
+  double* pot2 = U + TG_NT * N;
+  double* g2 = pot2 + 4 * N;
+  double* partial = g2 + 9 * N;
+  double* packed = partial + 2 * T_RB;
+  double* part = packed + Npad * 6;
+  const unsigned nb = (unsigned)std::min<int64_t>(4 * c->sm_count, lb_div_up(N, 256));
+  k_scale_h<<<lb_div_up(N, 256), 256, 0, c->stream>>>(N, c->H, z, h2z);
+  LB_LAUNCH(c);
+  CorrT c1{};
+  c1.nout = 3;
+  c1.kern[0] = LB_K_SP; c1.dens[0] = z; c1.out[0] = tp;
+  c1.kern[1] = LB_K_SPPDP; c1.dens[1] = z; c1.out[1] = tp + N;
+  c1.kern[2] = LB_K_SP; c1.dens[2] = h2z; c1.out[2] = tp + 2 * N;
+  LB_CHECK(pass_t<T_P1>(c, z, h2z, c1, tp));
+  k_sum_t<<<T_RB, 256, 0, c->stream>>>(N, z, partial);
+  LB_LAUNCH(c);
+  k_grad_avec<<<nb, 256, 0, c->stream>>>(N, gu, q1, z, h2z, tp, c->v1, c->w, partial, T_RB, c->area, av);
+  LB_LAUNCH(c);
+  const double* avs[6] = {av, av + N, av + 2 * N, av + 3 * N, h2z, z};
+  const double* bvs[6] = {sg, mu2, mu1, sg, mu2, mu2};
+  // S mu2 and S' mu2 (far + near), and the sums giving eta_z and W S mu2
+  LB_CHECK(lb_potentials(c, LB_FP64, mu2, pot2, (1u << LB_K_S) | (1u << LB_K_SP)));
+  k_tan_sums<<<T_RB, 256, 0, c->stream>>>(N, z, c->w, pot2 + (int64_t)LB_K_S * N, partial);
+  LB_LAUNCH(c);
+  // forward sums of w (sigma, mu1, mu2)
+  GradVecs gf{};
+  gf.v[0] = sg; gf.v[1] = mu1; gf.v[2] = mu2;
+  k_pack_g<<<lb_div_up(Npad, 256), 256, 0, c->stream>>>(N, Npad, 3, c->w, gf, packed);
+  LB_LAUNCH(c);
+  {
+    ProfScope prof(c, LB_PROF_SHAPE, N * N);
+    k_tan_fwd<<<dim3((unsigned)ntb, (unsigned)nsplit), GR_NTH, 0, c->stream>>>(
+        N, c->np, c->pos64, c->nrm64, packed, mt->flags, ntiles, c->row_ptr, c->near_patch, tps, part);
+    LB_LAUNCH(c);
+  }
+  lb_pair_counter += N * N;
+  k_reduce_tg<<<lb_div_up(N, 256), 256, 0, c->stream>>>(N, (int)nsplit, TG_NF, part, V);
+  LB_LAUNCH(c);
+  // transposed sums of a0 .. a5
+  GradVecs gt{};
+  for (int m = 0; m < 6; ++m) gt.v[m] = avs[m];
+  k_pack_g<<<lb_div_up(Npad, 256), 256, 0, c->stream>>>(N, Npad, 6, nullptr, gt, packed);
+  LB_LAUNCH(c);
+  {
+    ProfScope prof(c, LB_PROF_SHAPE, N * N);
+    k_tan_tr<<<dim3((unsigned)ntb, (unsigned)nsplit), GR_NTH, 0, c->stream>>>(
+        N, c->np, c->pos64, c->nrm64, packed, c->tflag, c->tmask, ntiles, tps, part);
+    LB_LAUNCH(c);
+  }
+  lb_pair_counter += N * N;
+  k_reduce_tg<<<lb_div_up(N, 256), 256, 0, c->stream>>>(N, (int)nsplit, TG_NT, part, U);
+  LB_LAUNCH(c);
+  TanIn in{};
+  for (int m = 0; m < 6; ++m) {
+    in.a[m] = avs[m];
+    in.b[m] = bvs[m];
+  }
+  in.V = V;
+  in.U = U;
+  in.z = z;
+  in.mu2 = mu2;
+  in.Smu2 = pot2 + (int64_t)LB_K_S * N;
+  in.Spmu2 = pot2 + (int64_t)LB_K_SP * N;
+  in.pf = pf;
+  in.partial = partial;
+  in.npart = T_RB;
+  k_tan_local<<<lb_div_up(N, 128), 128, 0, c->stream>>>(N, c->np, in, c->Xu, c->Xv, c->nrm, c->w, c->J, c->ginv,
+                                                         c->dref, c->dDu, c->dDv, c->area, gXu, gXv, g2);
+  LB_LAUNCH(c);
+  k_tan_diff<<<lb_div_up(N, 128), 128, 0, c->stream>>>(N, c->np, c->dDu, c->dDv, g2, gXu, gXv);
+  LB_LAUNCH(c);
+  return LB_OK;
+}

@@ -234,6 +234,10 @@ int lb_build_transpose(lb_ctx* c);
 // S^T g_u and z = A3^-T S^T S^T g_u (device, float64); grad [N][3]
 int lb_shape_grad_pairs(lb_ctx* c, const double* gu, const double* sg, const double* mu1, const double* mu2,
                         const double* q1, const double* z, double* grad);
+// gradient with respect to the tangents X_u, X_v (n, w, H through them), from
+// the projected right-hand side pf and the same vectors; gXu, gXv [N][3]
+int lb_tangent_grad_pairs(lb_ctx* c, const double* gu, const double* pf, const double* sg, const double* mu1,
+                          const double* mu2, const double* q1, const double* z, double* gXu, double* gXv);
 void lb_free_transpose(lb_ctx* c);
 int lb_get_mask(lb_ctx* c, int tb, int ts, MaskTable** out);
 // the same for sources of snp points per patch padded to nsrc_pad (the

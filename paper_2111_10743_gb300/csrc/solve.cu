@@ -1452,16 +1452,19 @@ extern "C" int lb_solve_lb_adjoint(lb_ctx* c, int nrhs, const double* gu, double
   return LB_OK;
 }
 
-// Node-position gradient of a loss of the A3 solve: sigma from A3 sigma = P f,
+// Geometry gradients of a loss of the A3 solve: sigma from A3 sigma = P f,
 // z from A3^T z = S^T S^T g_u (both float64 GMRES), then the gradient pair
-// sums of the adjoint module.
-extern "C" int lb_shape_gradient(lb_ctx* c, int nrhs, const double* f, const double* gu, double* grad,
-                                 lb_solve_info* info) {
+// sums of the adjoint module: node positions (grad) and/or tangents (gXu,
+// gXv); any output may be null.
+static int geometry_gradient(lb_ctx* c, int nrhs, const double* f, const double* gu, double* grad, double* gXu,
+                             double* gXv, lb_solve_info* info) {
   LB_CHECK(lb_require_corr(c));
-  if (c->far_order) return lb_fail(c, LB_EINVAL, "the node-position gradient uses the node rule: clear the far rule");
-  if (c->params.formulation != LB_A3) return lb_fail(c, LB_EINVAL, "the node-position gradient takes the A3 formulation");
+  if (c->far_order) return lb_fail(c, LB_EINVAL, "the geometry gradients use the node rule: clear the far rule");
+  if (c->params.formulation != LB_A3) return lb_fail(c, LB_EINVAL, "the geometry gradients take the A3 formulation");
   if (nrhs < 1) return lb_fail(c, LB_EINVAL, "nrhs must be >= 1");
-  if (!gu) return lb_fail(c, LB_EINVAL, "null input pointer");
+  if (!gu || !f) return lb_fail(c, LB_EINVAL, "null input pointer");
+  if (!grad && !gXu && !gXv) return lb_fail(c, LB_EINVAL, "no output requested");
+  if ((gXu == nullptr) != (gXv == nullptr)) return lb_fail(c, LB_EINVAL, "gXu and gXv come together");
   LB_CUDA(c, cudaSetDevice(c->device));
   const int64_t N = c->N;
   if (info) {
@@ -1472,9 +1475,22 @@ extern "C" int lb_shape_gradient(lb_ctx* c, int nrhs, const double* f, const dou
   lb_pair_counter = 0;
   lb_apply64_counter = lb_apply32_counter = 0;
   const double* df;
-  double* dgrad;
+  double* dgrad = nullptr;
   LB_CHECK(lb_stage_in(c, f, nrhs * N * sizeof(double), c->ws_stage_in, (const void**)&df));
-  LB_CHECK(lb_stage_out(c, grad, 3 * nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dgrad));
+  if (grad) LB_CHECK(lb_stage_out(c, grad, 3 * nrhs * N * sizeof(double), c->ws_stage_out, (void**)&dgrad));
+  // tangent outputs: the caller's device buffers, or a staging area in ws_bvec
+  double *dgu = nullptr, *dgv = nullptr;
+  const bool tan_host = gXu && (!lb_is_device_ptr(gXu) || !lb_is_device_ptr(gXv));
+  if (gXu) {
+    if (tan_host) {
+      LB_CHECK(lb_ensure(c, c->ws_bvec, (size_t)(6 * nrhs * N) * sizeof(double)));
+      dgu = (double*)c->ws_bvec.p;
+      dgv = dgu + 3 * nrhs * N;
+    } else {
+      dgu = gXu;
+      dgv = gXv;
+    }
+  }
   const bool gu_dev = lb_is_device_ptr(gu);
   // b, sigma, potentials [4], q1, t2, z, staged g_u
   LB_CHECK(lb_ensure(c, c->ws_shape, (size_t)(11 * N) * sizeof(double)));
@@ -1507,7 +1523,10 @@ extern "C" int lb_shape_gradient(lb_ctx* c, int nrhs, const double* f, const dou
     const int rc = gmres(c, LB_FP64, t2, z, c->params.tol, c->params.max_iter, &it2, &res2, nullptr);
     c->adjoint = false;
     LB_CHECK(rc);
-    LB_CHECK(lb_shape_grad_pairs(c, gr, sg, mu1, mu2, q1, z, dgrad + (int64_t)r * 3 * N));
+    if (dgrad) LB_CHECK(lb_shape_grad_pairs(c, gr, sg, mu1, mu2, q1, z, dgrad + (int64_t)r * 3 * N));
+    if (dgu)
+      LB_CHECK(lb_tangent_grad_pairs(c, gr, b, sg, mu1, mu2, q1, z, dgu + (int64_t)r * 3 * N,
+                                     dgv + (int64_t)r * 3 * N));
     if (info) {
       info->iterations += it1 + it2;
       const double res = std::max(res1, res2);
@@ -1519,7 +1538,12 @@ extern "C" int lb_shape_gradient(lb_ctx* c, int nrhs, const double* f, const dou
       }
     }
   }
-  LB_CHECK(lb_stage_out_finish(c, grad, dgrad, 3 * nrhs * N * sizeof(double)));
+  if (dgrad) LB_CHECK(lb_stage_out_finish(c, grad, dgrad, 3 * nrhs * N * sizeof(double)));
+  if (tan_host) {
+    LB_CUDA(c, cudaMemcpyAsync(gXu, dgu, 3 * nrhs * N * sizeof(double), cudaMemcpyDefault, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(gXv, dgv, 3 * nrhs * N * sizeof(double), cudaMemcpyDefault, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
   if (info) {
     info->pairs = lb_pair_counter;
     info->applies_fp64 = lb_apply64_counter;
@@ -1529,4 +1553,15 @@ extern "C" int lb_shape_gradient(lb_ctx* c, int nrhs, const double* f, const dou
                      c->params.tol, info->rel_residual);
   }
   return LB_OK;
+}
+
+extern "C" int lb_shape_gradient(lb_ctx* c, int nrhs, const double* f, const double* gu, double* grad,
+                                 lb_solve_info* info) {
+  if (!grad) return lb_fail(c, LB_EINVAL, "null output pointer");
+  return geometry_gradient(c, nrhs, f, gu, grad, nullptr, nullptr, info);
+}
+
+extern "C" int lb_geometry_gradient(lb_ctx* c, int nrhs, const double* f, const double* gu, double* gX,
+                                    double* gXu, double* gXv, lb_solve_info* info) {
+  return geometry_gradient(c, nrhs, f, gu, gX, gXu, gXv, info);
 }

@@ -1,9 +1,10 @@
 """The torch.autograd wrappers' plumbing, on the CPU.
 
-A stand-in context answers solve_lb, solve_lb_adjoint and shape_gradient
+A stand-in context answers solve_lb, solve_lb_adjoint and geometry_gradient
 from the oracle's dense FP64 matrices, so these tests check only what the
-wrappers add: which calls the backward pass makes, the sum of the
-node-position gradient over right-hand sides, and the shapes.  The library
+wrappers add: which calls the backward pass makes, the sums of the geometry
+gradients over right-hand sides, the shapes and the refusal of a surface that
+differs from the uploaded one.  The library
 calls themselves are checked against the oracle on the GPU.
 """
 import numpy as np
@@ -41,10 +42,30 @@ class OracleContext:
             self.cache[key] = shape_gradient_A3(self.d, f, gu)
         return self.cache[key]
 
-    def shape_gradient(self, f, gu, out):
-        self.calls.append("shape")
+    def tgrad(self, f, gu):
+        """The oracle's tangent gradient (dL/dX_u, dL/dX_v), cached."""
+        from oracle.shape import tangent_gradient_A3
+        key = ("t", f.tobytes(), gu.tobytes())
+        if key not in self.cache:
+            self.cache[key] = tangent_gradient_A3(self.d, f, gu)
+        return self.cache[key]
+
+    def check_geometry(self, **arrays):
+        g = self.d.geo
+        for k, a in arrays.items():
+            if a is not None and not np.array_equal(a.detach().numpy(), getattr(g, k)):
+                raise ValueError(f"{k} differs from the uploaded surface")
+
+    def geometry_gradient(self, f, gu, want_x, want_t, out):
+        self.calls.append("geometry")
         for r in range(f.shape[0]):
-            out[r] = torch.from_numpy(self.grad(f[r].numpy(), gu[r].numpy()))
+            fr, gr = f[r].numpy(), gu[r].numpy()
+            if want_x:
+                out[0][r] = torch.from_numpy(self.grad(fr, gr))
+            if want_t:
+                gxu, gxv = self.tgrad(fr, gr)
+                out[1][r] = torch.from_numpy(gxu)
+                out[2][r] = torch.from_numpy(gxv)
 
 
 @pytest.fixture(scope="module")
@@ -66,7 +87,7 @@ def test_solve_autograd_density_and_positions(octx):
     u = lb.solve_lb_autograd(f, octx, X=X)
     loss = ((u - ut) ** 2).sum()
     loss.backward()
-    assert octx.calls == ["solve", "adjoint", "shape"]
+    assert octx.calls == ["solve", "adjoint", "geometry"]
     gu = 2.0 * (u.detach() - ut).numpy()
     assert np.allclose(f.grad.numpy(), gu @ octx.L, rtol=0, atol=1e-12)
     ref = sum(octx.grad(f.detach()[r].numpy(), gu[r]) for r in range(2))
@@ -76,9 +97,37 @@ def test_solve_autograd_density_and_positions(octx):
     octx.calls.clear()
     f2 = f.detach()[:1]
     (lb.solve_lb_autograd(f2, octx, X=X) ** 2).sum().backward()
-    assert octx.calls == ["solve", "shape"]
+    assert octx.calls == ["solve", "geometry"]
     # without X the wrapper is the density-only one
     octx.calls.clear()
     g = torch.tensor(rng.standard_normal((1, N)), requires_grad=True)
     (lb.solve_lb_autograd(g, octx) ** 2).sum().backward()
     assert octx.calls == ["solve", "adjoint"]
+
+
+def test_solve_autograd_tangents_and_refusal(octx):
+    """Gradients with respect to the chart tangents come from the geometry
+    gradient, summed over right-hand sides; an X that differs from the
+    uploaded surface is refused before anything is solved."""
+    import paper_2111_10743_gb300 as lb
+    g = octx.d.geo
+    N = g.N
+    rng = np.random.default_rng(46)
+    f = torch.tensor(rng.standard_normal((2, N)))
+    Xu = torch.tensor(g.Xu.copy(), requires_grad=True)
+    Xv = torch.tensor(g.Xv.copy(), requires_grad=True)
+    ut = torch.tensor(rng.standard_normal((2, N)))
+    octx.calls.clear()
+    u = lb.solve_lb_autograd(f, octx, Xu=Xu, Xv=Xv)
+    ((u - ut) ** 2).sum().backward()
+    assert octx.calls == ["solve", "geometry"]
+    gu = 2.0 * (u.detach() - ut).numpy()
+    refs = [octx.tgrad(f[r].numpy(), gu[r]) for r in range(2)]
+    ru, rv = refs[0][0] + refs[1][0], refs[0][1] + refs[1][1]
+    assert np.abs(Xu.grad.numpy() - ru).max() < 1e-12 * np.abs(ru).max()
+    assert np.abs(Xv.grad.numpy() - rv).max() < 1e-12 * np.abs(rv).max()
+    X = torch.tensor(g.X + 1e-9, requires_grad=True)
+    octx.calls.clear()
+    with pytest.raises(ValueError, match="differs"):
+        lb.solve_lb_autograd(f, octx, X=X)
+    assert octx.calls == []

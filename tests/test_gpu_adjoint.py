@@ -128,3 +128,52 @@ def test_shape_gradient_matches_oracle(lb, name):
         with pytest.raises(lb.LBError) as e:
             ctx2.shape_gradient(f[:1], gu[:1])
         assert e.value.code == lb.LB_EINVAL
+
+
+@pytest.mark.parametrize("name", ["sphere300", "ellipsoid1200"])
+def test_geometry_gradient_matches_oracle(lb, name):
+    """Gradients of an A3-solve loss with respect to X, X_u and X_v
+    (corrections and near lists held fixed) against the oracle's dense
+    gradients, whose own pins check them against central differences."""
+    from oracle.shape import shape_gradient_A3, tangent_gradient_A3
+    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3, precision=lb.LB_FP64, tol=1e-14)
+    N = d.geo.N
+    rng = np.random.default_rng(47)
+    f = rng.standard_normal((2, N))
+    gu = rng.standard_normal((2, N))
+    gX, gXu, gXv, info = ctx.geometry_gradient(f, gu)
+    assert info["converged"] and gXu.shape == (2, N, 3)
+    for r in range(1 if name == "ellipsoid1200" else 2):
+        ru, rv = tangent_gradient_A3(d, f[r], gu[r])
+        assert _rel(gXu[r], ru) < 1e-9 and _rel(gXv[r], rv) < 1e-9
+        assert _rel(gX[r], shape_gradient_A3(d, f[r], gu[r])) < 1e-9
+    # tangents only: the same numbers
+    _, gXu2, gXv2, _ = ctx.geometry_gradient(f, gu, want_x=False)
+    assert np.array_equal(gXu2, gXu) and np.array_equal(gXv2, gXv)
+
+
+def test_autograd_geometry_path(lb):
+    """solve_lb_autograd with device tensors X, X_u, X_v: their gradients
+    against the oracle's, and an X that differs from the upload is refused."""
+    torch = pytest.importorskip("torch")
+    from oracle.shape import shape_gradient_A3, tangent_gradient_A3
+    ctx, s, d = ctx_for(lb, "sphere300", formulation=lb.LB_A3, precision=lb.LB_FP64, tol=1e-14)
+    g = d.geo
+    N = g.N
+    dev = "cuda"
+    rng = np.random.default_rng(48)
+    f = torch.tensor(rng.standard_normal((1, N)), device=dev, requires_grad=True)
+    ut = torch.tensor(rng.standard_normal((1, N)), device=dev)
+    X = torch.tensor(s.X, device=dev, requires_grad=True)
+    Xu = torch.tensor(s.Xu, device=dev, requires_grad=True)
+    Xv = torch.tensor(s.Xv, device=dev, requires_grad=True)
+    u = lb.solve_lb_autograd(f, ctx, X=X, Xu=Xu, Xv=Xv)
+    (0.5 * ((u - ut) ** 2).sum()).backward()
+    gu = (u.detach() - ut).cpu().numpy()[0]
+    fn = f.detach().cpu().numpy()[0]
+    assert _rel(X.grad.cpu().numpy(), shape_gradient_A3(d, fn, gu)) < 1e-9
+    ru, rv = tangent_gradient_A3(d, fn, gu)
+    assert _rel(Xu.grad.cpu().numpy(), ru) < 1e-9 and _rel(Xv.grad.cpu().numpy(), rv) < 1e-9
+    assert f.grad is not None
+    with pytest.raises(ValueError, match="differs"):
+        lb.solve_lb_autograd(f, ctx, X=X.detach() * (1.0 + 1e-12))
