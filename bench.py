@@ -25,7 +25,9 @@ the same right-hand side (fp64_plain) and reports the refined solution's
 error against a float64 solve to 1e-12 (err_vs_fp64).  cpu_baseline times
 the FP64 CPU oracle on the host cores: one full A3 apply, one S apply and the
 correction build of sampled rows, from which it estimates the oracle's time
-to solve with and without t_q.
+to solve with and without t_q.  torus_batch records the batched form: the
+18 right-hand sides of the torus (16 random f, 2 Hodge) solved in lockstep,
+beside one plain float64 solve of its first right-hand side.
 
 --impl reference times the FP64 CPU oracle (the tests' reference
 implementation) on the host cores instead, one full A3 apply per step.
@@ -366,10 +368,80 @@ def run_ours(args):
         "autotune": {k: v for k, v in ctx.get_tuning().items() if v},
         "clocks": clocks,
     }
+    if ws == 1 and args.case == "full" and not args.no_batch:
+        ctx.close()
+        out["torus_batch"] = torus_batch_record(lb, torch, local, stream, flush)
     if ws == 1 and not args.no_cpu_baseline and not args.case.startswith("torus"):
         iters64 = fp64_plain["iterations"] if fp64_plain else None
         out["cpu_baseline"] = cpu_baseline(iters64)
     print(json.dumps(out))
+
+
+def torus_batch_record(lb, torch, device, stream, flush, steps=3, warmup=3):
+    """The batched form on the torus R = 2, r = 0.75 (2,048 order-6 patches,
+    N = 57,344): 16 random Legendre f and the two Hodge right-hand sides
+    solved together in lockstep (A3, fp32_refined, tol 1e-10), timed like the
+    main line; beside it one plain float64 solve of its first right-hand side
+    (the float64 form solves right-hand sides one at a time, so 18 of them
+    cost 18 such solves) and that solution's error against the batch's."""
+    from workloads.configs import config
+    w = config(3)
+    s = w.surface
+    params = lb.default_params(eps_quad=1e-12, tol=1e-10, precision=lb.LB_FP32_REFINED, formulation=lb.LB_A3)
+    ctx = lb.Context(device, params, stream=stream)
+    ctx.upload_surface(s)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ctx.build_corrections()
+    torch.cuda.synchronize()
+    t_q = time.time() - t0
+    n, _, _ = ctx.get_geometry()
+    F = w.extra["F"]
+    fb = np.concatenate([w.f, ctx.surface_div(F[None]), -ctx.surface_div(np.cross(n, F)[None])])
+    f = torch.tensor(fb, device="cuda")
+    u = torch.empty_like(f)
+    for _ in range(warmup):
+        ctx.solve_lb(f, out=u)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    pairs = 0
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        _, info = ctx.solve_lb(f, out=u)
+        ev[k][1].record(stream)
+        pairs += info["pairs"]
+    torch.cuda.synchronize()
+    prof = ctx.get_profile()
+    ctx.set_profiling(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    cats = {k: v for k, v in prof.items() if isinstance(v, dict) and k.startswith("far")}
+    dom = max(cats, key=lambda k: cats[k]["ms"])
+    # one plain float64 solve of the first right-hand side, timed
+    ctx.set_params(lb.default_params(eps_quad=1e-12, tol=1e-10, precision=lb.LB_FP64, formulation=lb.LB_A3))
+    u64 = torch.empty_like(f[:1])
+    ctx.solve_lb(f[:1], out=u64)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, i64 = ctx.solve_lb(f[:1], out=u64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    err = float(torch.linalg.vector_norm(u[:1] - u64) / torch.linalg.vector_norm(u64))
+    ctx.close()
+    return {
+        "workload": WORKLOAD_TORUS.format(P=s.npatch, N=s.N), "nrhs": int(fb.shape[0]), "steps": steps,
+        "ms_per_step": round(ms, 2), "value": round(pairs / steps / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+        "t_q_s": round(t_q, 2), "iterations": info["iterations"], "refinements": info["refinements"],
+        "rel_residual": info["rel_residual"], "graph_iterations": info["graph_iterations"],
+        "dominant_kernel": {"name": dom, "ms_per_step": round(cats[dom]["ms"] / steps, 3),
+                            "calls_per_step": cats[dom]["calls"] / steps},
+        "fp64_plain_one_rhs_ms": round(ms64, 2), "fp64_plain_iterations": i64["iterations"],
+        "fp64_plain_all_rhs_est_ms": round(ms64 * fb.shape[0], 1),
+        "speedup_of_batch_est": round(ms64 * fb.shape[0] / ms, 2),
+        "err_vs_fp64_first_rhs": err,
+    }
 
 
 def cpu_model() -> str:
@@ -508,6 +580,7 @@ def main():
     ap.add_argument("--precision", default="fp32_refined", choices=["fp32_refined", "fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 solve after the timed region")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched torus record of the default line")
     ap.add_argument("--case", default="full", choices=["full", "small", "torus_batch", "torus_small"],
                     help="full: the benchmark surface; small: 320 patches of the same kind (profiling); "
                          "torus_batch: the torus with 18 right-hand sides solved in lockstep; "

@@ -352,7 +352,12 @@ int lb_geometry_gradient(lb_ctx* ctx, int nrhs, const double* f, const double* g
  * keep the fastest): shapes[8], indexed by precision (0 float32, 1
  * double-float) * 4 + pass (0: A3 pass 1, 1: pass 2) * 2 + (0: 4 densities,
  * 1: 8 densities per pass).  Values: 0 = 128 threads x 64-source tiles,
- * 1 = 128 x 128, 2 = 256 x 64, -1 = not tuned yet.  Host memory. */
+ * 1 = 128 x 128, 2 = 256 x 64, -1 = not tuned yet.  shapes[8 + kind], kind
+ * 0..3 = K1 (S, grad S), all four kernels, A3 pass 2, A2 pass 2: the
+ * variant chosen by timing for single-density float32 passes (K1: 0 scalar,
+ * 1 two sources per packed instruction; the others: 0 packed, 1 packed with
+ * registers capped for three resident blocks per SM), -1 = not tuned yet.
+ * shapes: host memory of 12 ints. */
 int lb_get_tuning(lb_ctx* ctx, int* shapes);
 
 /* Far-field sums of one density that allocate nothing: the float32 pair

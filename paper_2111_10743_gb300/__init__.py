@@ -213,7 +213,7 @@ class Context:
 
     def get_tuning(self) -> dict:
         """Launch shapes picked by the batched passes' tuner (-1: not tuned)."""
-        a = (ctypes.c_int * 8)()
+        a = (ctypes.c_int * 12)()
         self._check(_lib.lb_get_tuning(self._h, a))
         names = {0: "128x64", 1: "128x128", 2: "256x64", -1: None}
         out = {}
@@ -221,6 +221,11 @@ class Context:
             for k, kn in enumerate(("k1", "k2")):
                 for r, rn in enumerate(("rc4", "rc8")):
                     out[f"{pn}_{kn}_{rn}"] = names[a[p * 4 + k * 2 + r]]
+        single = {0: ("scalar", "packed"), 1: ("packed", "packed_3blocks"), 2: ("packed", "packed_3blocks"),
+                  3: ("packed", "packed_3blocks")}
+        for kind, kn in enumerate(("k1", "kall", "k2", "k4")):
+            v = a[8 + kind]
+            out[f"far32_single_{kn}"] = single[kind][v] if v >= 0 else None
         return out
 
     def get_profile(self) -> dict:

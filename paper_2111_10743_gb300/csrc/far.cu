@@ -34,7 +34,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "dfloat.cuh"
@@ -284,8 +286,8 @@ __device__ __forceinline__ void pair2(const u64* T, const u64* S, u64* acc, cons
   }
 }
 
-template <int KIND, int NT, int NTH, int TS>
-__global__ void __launch_bounds__(NTH) k_far32x2(int64_t N, int np, const float4* __restrict__ tpos,
+template <int KIND, int NT, int NTH, int TS, int MINB = 1>
+__global__ void __launch_bounds__(NTH, MINB) k_far32x2(int64_t N, int np, const float4* __restrict__ tpos,
                                                  const float4* __restrict__ tnrm, const float4* __restrict__ srcA,
                                                  const float4* __restrict__ srcB, const uint8_t* __restrict__ flags,
                                                  int64_t ntiles, const int64_t* __restrict__ row_ptr,
@@ -458,11 +460,10 @@ static int launch_far_t(lb_ctx* c, const void* srcA, const void* srcB, double* p
   MaskTable* m = nullptr;
   LB_CHECK(lb_get_mask_src(c, tb, TS, snp, src_pad(c), &m));
   const int64_t ntb = m->ntb, ntiles = m->ntiles;
-  // enough CTAs for several per SM: split the source range
-  const int64_t want = 6LL * c->sm_count;
-  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(ntiles, (want + ntb - 1) / ntb));
+  // split the source range so that the grid fills whole waves
+  int nsplit = 1;
+  LB_CHECK(lb_pick_nsplit(c, k_far<R, KIND, NT, NTH, TS>, NTH, ntb, ntiles, &nsplit));
   const int tps = (int)((ntiles + nsplit - 1) / nsplit);
-  nsplit = (ntiles + tps - 1) / tps;
   const V4* tp = sizeof(R) == 4 ? (const V4*)c->pos32 : (const V4*)c->pos64;
   const V4* tn = sizeof(R) == 4 ? (const V4*)c->nrm32 : (const V4*)c->nrm64;
   dim3 grid((unsigned)ntb, (unsigned)nsplit);
@@ -476,26 +477,112 @@ static int launch_far_t(lb_ctx* c, const void* srcA, const void* srcB, double* p
   return LB_OK;
 }
 
-template <int KIND, int NT, int NTH, int TS>
+template <int KIND, int NT, int NTH, int TS, int MINB = 1>
 static int launch_far32x2(lb_ctx* c, const void* srcA, const void* srcB, double* part, int* nsplit_out) {
   const int tb = NT * NTH;
   if (c->np * 62 < TS) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
   MaskTable* m = nullptr;
   LB_CHECK(lb_get_mask(c, tb, TS, &m));
   const int64_t ntb = m->ntb, ntiles = m->ntiles;
-  const int64_t want = 6LL * c->sm_count;
-  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(ntiles, (want + ntb - 1) / ntb));
+  int nsplit = 1;
+  LB_CHECK(lb_pick_nsplit(c, k_far32x2<KIND, NT, NTH, TS, MINB>, NTH, ntb, ntiles, &nsplit));
   const int tps = (int)((ntiles + nsplit - 1) / nsplit);
-  nsplit = (ntiles + tps - 1) / tps;
   dim3 grid((unsigned)ntb, (unsigned)nsplit);
   ProfScope prof(c, LB_PROF_FAR32_K1 + KIND, c->N * c->N);
-  k_far32x2<KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, c->np, c->pos32, c->nrm32, (const float4*)srcA,
+  k_far32x2<KIND, NT, NTH, TS, MINB><<<grid, NTH, 0, c->stream>>>(c->N, c->np, c->pos32, c->nrm32, (const float4*)srcA,
                                                             (const float4*)srcB, m->flags, ntiles, c->row_ptr,
                                                             c->near_patch, tps, part);
   LB_LAUNCH(c);
   lb_pair_counter += c->N * c->N;
   *nsplit_out = (int)nsplit;
   return LB_OK;
+}
+
+// Single-density float32 passes: two launch variants per kind, chosen by
+// timing.  K1: the scalar kernel (variant 0) or the packed two-source kernel
+// (1); the longer kinds: the packed kernel at its natural register count (0)
+// or capped for three resident blocks per SM (1).
+static int launch_fp32(lb_ctx* c, int kind, int variant, const void* A, const void* B, double* part, int* ns) {
+  switch (kind) {
+    case FAR_K1:
+      return variant ? launch_far32x2<FAR_K1, 4, 128, 128>(c, A, B, part, ns)
+                     : launch_far_t<float, FAR_K1, 4, 128, 128>(c, A, B, part, ns);
+    case FAR_KALL:
+      return variant ? launch_far32x2<FAR_KALL, 4, 128, 128, 3>(c, A, B, part, ns)
+                     : launch_far32x2<FAR_KALL, 4, 128, 128>(c, A, B, part, ns);
+    case FAR_K2:
+      return variant ? launch_far32x2<FAR_K2, 4, 128, 128, 3>(c, A, B, part, ns)
+                     : launch_far32x2<FAR_K2, 4, 128, 128>(c, A, B, part, ns);
+    default:
+      return variant ? launch_far32x2<FAR_K4, 4, 128, 128, 3>(c, A, B, part, ns)
+                     : launch_far32x2<FAR_K4, 4, 128, 128>(c, A, B, part, ns);
+  }
+}
+
+namespace {
+struct SingleKey {
+  int device;
+  int64_t N;
+  int np, kind;
+  bool operator<(const SingleKey& o) const {
+    return std::tie(device, N, np, kind) < std::tie(o.device, o.N, o.np, o.kind);
+  }
+};
+std::mutex g_single_mu;
+std::map<SingleKey, int> g_single;
+}  // namespace
+
+// The variant for this pass: tuned earlier in the process, or timed now on
+// the caller's data (each variant launched twice, the second timed; nothing
+// is counted or profiled), or variant 0 inside a stream capture.
+static int fp32_variant(lb_ctx* c, int kind, const void* A, const void* B, double* part, int* variant) {
+  if (c->far_order) { *variant = 0; return LB_OK; }  // oversampled sources: the scalar kernels
+  const SingleKey key{c->device, c->N, c->np, kind};
+  {
+    std::lock_guard<std::mutex> lk(g_single_mu);
+    auto it = g_single.find(key);
+    if (it != g_single.end()) { *variant = it->second; return LB_OK; }
+  }
+  *variant = 0;
+  if (c->capturing) return LB_OK;
+  const int prof = c->prof_on;
+  const int64_t pairs = lb_pair_counter, launches = c->launches;
+  c->prof_on = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = LB_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    rc = lb_fail(c, LB_ECUDA, "cudaEventCreate failed");
+  float best_ms = 1e30f;
+  int best = 0;
+  for (int v = 0; v < 2 && rc == LB_OK; ++v) {
+    int ns = 0;
+    rc = launch_fp32(c, kind, v, A, B, part, &ns);  // warm-up (module load, occupancy query)
+    if (rc == LB_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = lb_fail(c, LB_ECUDA, "event record");
+    if (rc == LB_OK) rc = launch_fp32(c, kind, v, A, B, part, &ns);
+    if (rc == LB_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) rc = lb_fail(c, LB_ECUDA, "event record");
+    float ms = 0.f;
+    if (rc == LB_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      rc = lb_fail(c, LB_ECUDA, "timing a far-field launch variant failed");
+    if (rc == LB_OK && ms < best_ms) { best_ms = ms; best = v; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->prof_on = prof;
+  lb_pair_counter = pairs;
+  c->launches = launches;
+  if (rc != LB_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_single_mu);
+    g_single[key] = best;
+  }
+  *variant = best;
+  return LB_OK;
+}
+
+int lb_far_tuned_variant(lb_ctx* c, int kind) {
+  std::lock_guard<std::mutex> lk(g_single_mu);
+  auto it = g_single.find(SingleKey{c->device, c->N, c->np, kind});
+  return it == g_single.end() ? -1 : it->second;
 }
 
 int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* srcB, double* part, int* nsplit) {
@@ -516,12 +603,9 @@ int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* s
       default: return launch_far_t<double, FAR_K4, 2, 128, 64>(c, srcA, srcB, part, nsplit);
     }
   }
-  switch (kind) {
-    case FAR_K1: return launch_far_t<float, FAR_K1, 4, 128, 128>(c, srcA, srcB, part, nsplit);
-    case FAR_KALL: return launch_far32x2<FAR_KALL, 4, 128, 128>(c, srcA, srcB, part, nsplit);
-    case FAR_K2: return launch_far32x2<FAR_K2, 4, 128, 128>(c, srcA, srcB, part, nsplit);
-    default: return launch_far32x2<FAR_K4, 4, 128, 128>(c, srcA, srcB, part, nsplit);
-  }
+  int variant = 0;
+  LB_CHECK(fp32_variant(c, kind, srcA, srcB, part, &variant));
+  return launch_fp32(c, kind, variant, srcA, srcB, part, nsplit);
 }
 
 // ---------------------------------------------------------------------------
@@ -590,11 +674,15 @@ __device__ __forceinline__ double to_d(F2 v) { return df_to_double(v); }
 // double-float (weights vh + vl, densities dh + dl); float64 throughput on
 // GB300 is a small fraction of float32, and the float32 / double-float sums
 // match the accuracy of the pair sums they complete.
+// The float copies are padded to npv float4 vectors per (block, kernel) and
+// per patch (lb_lowp_vals, lowp_dens: zeros past np), so that every lane
+// moves four nodes' weights and densities with single 16-byte loads; the
+// rows are streamed, four vectors per lane in flight.
 template <int MODE>
-__global__ void k_epilogue(int64_t N, int np, int nsplit, int nacc, const double* __restrict__ part,
+__global__ void k_epilogue(int64_t N, int np, int npv, int nsplit, int nacc, const double* __restrict__ part,
                            const double* __restrict__ nrm, const int64_t* __restrict__ row_ptr,
                            const int32_t* __restrict__ near_patch, const double* __restrict__ vals,
-                           const float* __restrict__ vh, const float* __restrict__ vl, EpiSpec sp) {
+                           const float4* __restrict__ vh, const float4* __restrict__ vl, EpiSpec sp) {
   using T = typename std::conditional<MODE == 0, double, typename std::conditional<MODE == 1, float, F2>::type>::type;
   const int lane = threadIdx.x & 31;
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -603,7 +691,51 @@ __global__ void k_epilogue(int64_t N, int np, int nsplit, int nacc, const double
 #pragma unroll
   for (int o = 0; o < 4; ++o) cs[o] = T{};
   const bool corr = MODE == 0 ? vals != nullptr : vh != nullptr;
-  if (corr) {
+  if constexpr (MODE != 0) {
+   if (corr) {
+    const int64_t rb = row_ptr[i];
+    const int tot = (int)(row_ptr[i + 1] - rb) * npv;
+    for (int e0 = lane; e0 < tot; e0 += 128) {
+      int64_t bq[4], pq[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + 32 * u;
+        const int bl = e < tot ? e / npv : 0;
+        const int qv = e < tot ? e - bl * npv : 0;
+        bq[u] = (rb + bl) * (LB_NKERNELS * (int64_t)npv) + qv;        // weights of kernel 0
+        pq[u] = e < tot ? (int64_t)near_patch[rb + bl] * npv + qv : -1;  // densities
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (pq[u] < 0) continue;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          if (o >= sp.nout || sp.kern[o] < 0) continue;
+          const int64_t wi = bq[u] + sp.kern[o] * (int64_t)npv;
+          const float4 w = __ldg(vh + wi);
+          const float4 x = __ldg(reinterpret_cast<const float4*>(sp.dh[o]) + pq[u]);
+          if constexpr (MODE == 1) {
+            float t = cs[o];
+            t = fmaf(w.x, x.x, t);
+            t = fmaf(w.y, x.y, t);
+            t = fmaf(w.z, x.z, t);
+            t = fmaf(w.w, x.w, t);
+            cs[o] = t;
+          } else {
+            const float4 wl = __ldg(vl + wi);
+            const float4 xl = __ldg(reinterpret_cast<const float4*>(sp.dl[o]) + pq[u]);
+            df_acc(cs[o], df_mul({w.x, wl.x}, {x.x, xl.x}));
+            df_acc(cs[o], df_mul({w.y, wl.y}, {x.y, xl.y}));
+            df_acc(cs[o], df_mul({w.z, wl.z}, {x.z, xl.z}));
+            df_acc(cs[o], df_mul({w.w, wl.w}, {x.w, xl.w}));
+          }
+        }
+      }
+    }
+    warp_reduce_scatter<4>(cs, lane);  // lane 8 o holds output o
+  }
+  } else {
+   if (corr) {
     // the row's (block, node) pairs flattened; each lane walks them 32 apart,
     // four at a time so that their loads overlap, tracking (block, node)
     // incrementally instead of dividing
@@ -635,16 +767,12 @@ __global__ void k_epilogue(int64_t N, int np, int nsplit, int nacc, const double
         for (int o = 0; o < 4; ++o) {
           if (o >= sp.nout || sp.kern[o] < 0) continue;
           const int64_t w = vo[u] + sp.kern[o] * np;
-          if constexpr (MODE == 0)
-            cs[o] = fma(__ldg(vals + w), sp.dens[o][col[u]], cs[o]);
-          else if constexpr (MODE == 1)
-            cs[o] = fmaf(__ldg(vh + w), sp.dh[o][col[u]], cs[o]);
-          else
-            df_acc(cs[o], df_mul({__ldg(vh + w), __ldg(vl + w)}, {sp.dh[o][col[u]], sp.dl[o][col[u]]}));
+          if constexpr (MODE == 0) cs[o] = fma(__ldg(vals + w), sp.dens[o][col[u]], cs[o]);
         }
       }
     }
     warp_reduce_scatter<4>(cs, lane);  // lane 8 o holds output o
+  }
   }
   // split partials of output o summed by lanes 8 o .. 8 o + 7, eight splits
   // apart (float64 for float64 passes, else (hi, lo) float pairs summed in
@@ -698,20 +826,45 @@ int lb_split_f64(lb_ctx* c, int64_t n, const double* x, float* hi, float* lo) {
   return LB_OK;
 }
 
-// float32 hi / lo copies of the correction weights, made on first use after
-// the corrections were loaded or built
-int lb_lowp_vals(lb_ctx* c) {
-  if (!c->have_corr || c->vals_hi) return LB_OK;
-  const int64_t n = c->nnzb * LB_NKERNELS * c->np;
-  LB_CHECK(lb_alloc(c, &c->vals_hi, (size_t)n));
-  LB_CHECK(lb_alloc(c, &c->vals_lo, (size_t)n));
-  return lb_split_f64(c, n, c->vals, c->vals_hi, c->vals_lo);
+// hi = (float)x, lo = (float)(x - hi) of rows of np values into rows of npp
+// (the tail of each row zero): n_rows rows
+__global__ void k_split_pad(int64_t nrows, int np, int npp, const double* __restrict__ x, float* __restrict__ hi,
+                            float* __restrict__ lo) {
+  const int64_t n = nrows * npp;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / npp;
+    const int q = (int)(t - r * npp);
+    const double v = q < np ? x[r * np + q] : 0.0;
+    const float h = (float)v;
+    hi[t] = h;
+    if (lo) lo[t] = (float)(v - (double)h);
+  }
 }
 
-// float32 / double-float copies of the distinct correction densities of sp
+static int split_pad(lb_ctx* c, int64_t nrows, const double* x, float* hi, float* lo) {
+  const int npp = lb_np_pad(c->np);
+  const unsigned nb = (unsigned)std::min<int64_t>(8LL * c->sm_count, std::max<int64_t>(1, lb_div_up(nrows * npp, 256)));
+  k_split_pad<<<nb, 256, 0, c->stream>>>(nrows, c->np, npp, x, hi, lo);
+  LB_LAUNCH(c);
+  return LB_OK;
+}
+
+// float32 hi / lo copies of the correction weights, [nnzb][4][npp] with the
+// node index padded to a multiple of four, made on first use after the
+// corrections were loaded or built
+int lb_lowp_vals(lb_ctx* c) {
+  if (!c->have_corr || c->vals_hi) return LB_OK;
+  const int64_t n = c->nnzb * LB_NKERNELS * lb_np_pad(c->np);
+  LB_CHECK(lb_alloc(c, &c->vals_hi, (size_t)n));
+  LB_CHECK(lb_alloc(c, &c->vals_lo, (size_t)n));
+  return split_pad(c, c->nnzb * LB_NKERNELS, c->vals, c->vals_hi, c->vals_lo);
+}
+
+// float32 / double-float copies of the distinct correction densities of sp,
+// [npatch][npp] each
 static int lowp_dens(lb_ctx* c, int mode, EpiSpec& sp) {
-  const int64_t N = c->N;
-  LB_CHECK(lb_ensure(c, c->ws_dlow, (size_t)(8 * N) * sizeof(float)));
+  const int64_t M = c->npatch * lb_np_pad(c->np);
+  LB_CHECK(lb_ensure(c, c->ws_dlow, (size_t)(8 * M) * sizeof(float)));
   float* base = (float*)c->ws_dlow.p;
   const double* uniq[4];
   int nu = 0;
@@ -721,10 +874,10 @@ static int lowp_dens(lb_ctx* c, int mode, EpiSpec& sp) {
     while (j < nu && uniq[j] != sp.dens[o]) ++j;
     if (j == nu) {
       uniq[nu++] = sp.dens[o];
-      LB_CHECK(lb_split_f64(c, N, sp.dens[o], base + 2 * j * N, mode == 2 ? base + (2 * j + 1) * N : nullptr));
+      LB_CHECK(split_pad(c, c->npatch, sp.dens[o], base + 2 * j * M, mode == 2 ? base + (2 * j + 1) * M : nullptr));
     }
-    sp.dh[o] = base + 2 * j * N;
-    sp.dl[o] = base + (2 * j + 1) * N;
+    sp.dh[o] = base + 2 * j * M;
+    sp.dl[o] = base + (2 * j + 1) * M;
   }
   return LB_OK;
 }
@@ -739,15 +892,18 @@ static int run_epilogue(lb_ctx* c, int prec, int nsplit, int nacc, const double*
     LB_CHECK(lowp_dens(c, mode, sp));
   }
   ProfScope prof(c, LB_PROF_EPILOGUE);
+  const int npv = lb_np_pad(c->np) / 4;
+  const float4* vh = corr ? (const float4*)c->vals_hi : nullptr;
+  const float4* vl = corr ? (const float4*)c->vals_lo : nullptr;
   if (mode == 0)
-    k_epilogue<0><<<grid, 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr, c->near_patch,
-                                               corr ? c->vals : nullptr, nullptr, nullptr, sp);
+    k_epilogue<0><<<grid, 256, 0, c->stream>>>(c->N, c->np, npv, nsplit, nacc, part, c->nrm, c->row_ptr,
+                                               c->near_patch, corr ? c->vals : nullptr, nullptr, nullptr, sp);
   else if (mode == 1)
-    k_epilogue<1><<<grid, 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr, c->near_patch,
-                                               nullptr, corr ? c->vals_hi : nullptr, nullptr, sp);
+    k_epilogue<1><<<grid, 256, 0, c->stream>>>(c->N, c->np, npv, nsplit, nacc, part, c->nrm, c->row_ptr,
+                                               c->near_patch, nullptr, vh, nullptr, sp);
   else
-    k_epilogue<2><<<grid, 256, 0, c->stream>>>(c->N, c->np, nsplit, nacc, part, c->nrm, c->row_ptr, c->near_patch,
-                                               nullptr, corr ? c->vals_hi : nullptr, corr ? c->vals_lo : nullptr, sp);
+    k_epilogue<2><<<grid, 256, 0, c->stream>>>(c->N, c->np, npv, nsplit, nacc, part, c->nrm, c->row_ptr,
+                                               c->near_patch, nullptr, vh, vl, sp);
   LB_LAUNCH(c);
   return LB_OK;
 }
@@ -755,7 +911,7 @@ static int run_epilogue(lb_ctx* c, int prec, int nsplit, int nacc, const double*
 static int part_buffer(lb_ctx* c, double** part) {
   // up to 4 accumulators x up to ntiles splits
   const int64_t max_split = src_pad(c) / 64;
-  const int64_t want = std::min<int64_t>(max_split, 6LL * c->sm_count + 8);
+  const int64_t want = std::min<int64_t>(max_split, 32);
   LB_CHECK(lb_ensure(c, c->ws_part, (size_t)(want * 4 * c->N) * sizeof(double)));
   *part = (double*)c->ws_part.p;
   return LB_OK;
@@ -965,13 +1121,13 @@ extern "C" int lb_far_sums(lb_ctx* c, int precision, int nrhs, const double* sig
     }
     const unsigned grid = lb_div_up(N * 32, 256);
     if (precision == LB_FP64)
-      k_epilogue<0><<<grid, 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr, c->near_patch, nullptr,
+      k_epilogue<0><<<grid, 256, 0, c->stream>>>(N, c->np, 1, nsplit, 4, part, c->nrm, c->row_ptr, c->near_patch, nullptr,
                                                  nullptr, nullptr, sp);
     else if (precision == LB_FP32)
-      k_epilogue<1><<<grid, 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr, c->near_patch, nullptr,
+      k_epilogue<1><<<grid, 256, 0, c->stream>>>(N, c->np, 1, nsplit, 4, part, c->nrm, c->row_ptr, c->near_patch, nullptr,
                                                  nullptr, nullptr, sp);
     else
-      k_epilogue<2><<<grid, 256, 0, c->stream>>>(N, c->np, nsplit, 4, part, c->nrm, c->row_ptr, c->near_patch, nullptr,
+      k_epilogue<2><<<grid, 256, 0, c->stream>>>(N, c->np, 1, nsplit, 4, part, c->nrm, c->row_ptr, c->near_patch, nullptr,
                                                  nullptr, nullptr, sp);
     LB_LAUNCH(c);
   }
@@ -1151,7 +1307,7 @@ extern "C" int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, cons
     sp.kern[k] = -1;
     sp.out[k] = out + (int64_t)k * N;
   }
-  k_epilogue<1><<<lb_div_up(N * 32, 256), 256, 0, st>>>(N, np, (int)nsplit, 4, part, nrm, row_ptr, near_patch,
+  k_epilogue<1><<<lb_div_up(N * 32, 256), 256, 0, st>>>(N, np, 1, (int)nsplit, 4, part, nrm, row_ptr, near_patch,
                                                         nullptr, nullptr, nullptr, sp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return lb_fail(nullptr, LB_ECUDA, "lb_far_sums_noalloc launch: %s", cudaGetErrorString(e));

@@ -318,8 +318,8 @@ __global__ void k_packqdf(int64_t N, int64_t Npad, int R, int RC, int npl, const
 template <int RC, bool PASS2, int MODE>
 __global__ void k_epib(int64_t N, int np, int R, int nsplit, const double* __restrict__ part,
                        const double* __restrict__ nrm, const int64_t* __restrict__ row_ptr,
-                       const int32_t* __restrict__ near_patch, const float* __restrict__ vh,
-                       const float* __restrict__ vl, const float4* __restrict__ D, double* __restrict__ out0,
+                       const int32_t* __restrict__ near_patch, const float4* __restrict__ vh,
+                       const float4* __restrict__ vl, const float4* __restrict__ D, double* __restrict__ out0,
                        double* __restrict__ out1, double* __restrict__ out2, double* __restrict__ out3) {
   using T = typename std::conditional<MODE == 1, float, F2>::type;
   constexpr int NK = PASS2 ? 4 : 2;
@@ -334,10 +334,16 @@ __global__ void k_epib(int64_t N, int np, int R, int nsplit, const double* __res
   T cs[V];
 #pragma unroll
   for (int k = 0; k < V; ++k) cs[k] = T{};
+  // the row's (block, node) pairs flattened; each lane walks them 32 apart,
+  // so that a warp reads 32 consecutive nodes' densities per load; the float
+  // weights are stored [block][kernel][npp], npp = np rounded up to four
+  const int npp = (np + 3) & ~3;
   const int64_t rb = row_ptr[i];
   const int ne = (int)((row_ptr[i + 1] - rb) * np);
-  const int stride = LB_NKERNELS * np;
+  const int64_t stride = LB_NKERNELS * (int64_t)npp;
   int bo = lane / np, q = lane - (lane / np) * np;
+  const float* vhf = reinterpret_cast<const float*>(vh);
+  const float* vlf = reinterpret_cast<const float*>(vl);
   for (int e = lane; e < ne; e += 32) {
     const int64_t b = rb + bo;
     const int64_t col = (int64_t)near_patch[b] * np + q;
@@ -349,8 +355,8 @@ __global__ void k_epib(int64_t N, int np, int R, int nsplit, const double* __res
       dv[4 * g] = v.x; dv[4 * g + 1] = v.y; dv[4 * g + 2] = v.z; dv[4 * g + 3] = v.w;
     }
     if constexpr (MODE == 1) {
-      const float wS = __ldg(vh + wo + LB_K_S * np), wSp = __ldg(vh + wo + LB_K_SP * np);
-      const float wSD = PASS2 ? __ldg(vh + wo + LB_K_SPPDP * np) : 0.f;
+      const float wS = __ldg(vhf + wo + LB_K_S * npp), wSp = __ldg(vhf + wo + LB_K_SP * npp);
+      const float wSD = PASS2 ? __ldg(vhf + wo + LB_K_SPPDP * npp) : 0.f;
       float* c = cs;
 #pragma unroll
       for (int r = 0; r < RC; ++r) {
@@ -367,10 +373,10 @@ __global__ void k_epib(int64_t N, int np, int R, int nsplit, const double* __res
         }
       }
     } else {
-      const F2 wS = {__ldg(vh + wo + LB_K_S * np), __ldg(vl + wo + LB_K_S * np)};
-      const F2 wSp = {__ldg(vh + wo + LB_K_SP * np), __ldg(vl + wo + LB_K_SP * np)};
+      const F2 wS = {__ldg(vhf + wo + LB_K_S * npp), __ldg(vlf + wo + LB_K_S * npp)};
+      const F2 wSp = {__ldg(vhf + wo + LB_K_SP * npp), __ldg(vlf + wo + LB_K_SP * npp)};
       F2 wSD = {0.f, 0.f};
-      if (PASS2) wSD = {__ldg(vh + wo + LB_K_SPPDP * np), __ldg(vl + wo + LB_K_SPPDP * np)};
+      if (PASS2) wSD = {__ldg(vhf + wo + LB_K_SPPDP * npp), __ldg(vlf + wo + LB_K_SPPDP * npp)};
       F2* c = cs;
 #pragma unroll
       for (int r = 0; r < RC; ++r) {
@@ -480,37 +486,6 @@ struct BShape {
 };
 static const BShape kShapes[3] = {{128, 64}, {128, 128}, {256, 64}};
 
-template <typename F>
-static int pick_nsplit(lb_ctx* c, F kernel, int nth, int64_t ntb, int64_t ntiles, int* out) {
-  // queried once per kernel: the launches of a captured iteration make no queries
-  int per_sm = 0;
-  auto it = c->occupancy.find((const void*)kernel);
-  if (it != c->occupancy.end()) {
-    per_sm = it->second;
-  } else {
-    LB_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nth, 0));
-    c->occupancy[(const void*)kernel] = per_sm;
-  }
-  const int64_t slots = (int64_t)std::max(per_sm, 1) * c->sm_count;
-  int best = 1;
-  double best_eff = -1;
-  const int64_t hi = std::min<int64_t>(ntiles, 32);
-  for (int64_t s = 1; s <= hi; ++s) {
-    const int64_t tps = (ntiles + s - 1) / s;
-    const int64_t ns = (ntiles + tps - 1) / tps;
-    const int64_t blocks = ntb * ns;
-    const double waves = (double)blocks / (double)slots;
-    const double eff = waves / std::ceil(waves);
-    if (eff > best_eff + 0.02) {
-      best_eff = eff;
-      best = (int)ns;
-    }
-    if (eff > 0.97 && blocks >= slots) break;
-  }
-  *out = best;
-  return LB_OK;
-}
-
 // largest split count a batched launch can pick (workspace sizing)
 static int64_t max_nsplit(lb_ctx* c) { return std::min<int64_t>(c->Npad / 64, 32); }
 
@@ -524,7 +499,7 @@ static int far_shape(lb_ctx* c, bool df, const void* G, const void* Q, double* p
   int nsplit = 1;
   if (!df) {
     auto kern = k_farb32<KIND, RC, NTH, TS>;
-    LB_CHECK(pick_nsplit(c, kern, NTH, ntb, ntiles, &nsplit));
+    LB_CHECK(lb_pick_nsplit(c, kern, NTH, ntb, ntiles, &nsplit));
     const int tps = (int)((ntiles + nsplit - 1) / nsplit);
     ProfScope prof(c, cat, pairs);
     kern<<<dim3((unsigned)ntb, (unsigned)nsplit), NTH, 0, c->stream>>>(
@@ -532,7 +507,7 @@ static int far_shape(lb_ctx* c, bool df, const void* G, const void* Q, double* p
     LB_LAUNCH(c);
   } else {
     auto kern = k_farbdf<KIND, RC, NTH, TS>;
-    LB_CHECK(pick_nsplit(c, kern, NTH, ntb, ntiles, &nsplit));
+    LB_CHECK(lb_pick_nsplit(c, kern, NTH, ntb, ntiles, &nsplit));
     const int tps = (int)((ntiles + nsplit - 1) / nsplit);
     ProfScope prof(c, cat, pairs);
     kern<<<dim3((unsigned)ntb, (unsigned)nsplit), NTH, 0, c->stream>>>(
@@ -671,12 +646,14 @@ static int run_epib(lb_ctx* c, int prec, int R, int nsplit, const double* part, 
   const unsigned eb = lb_div_up(N * 32, 256);
   const float4* D = (const float4*)c->ws_dlow.p;
   ProfScope prof(c, LB_PROF_EPILOGUE);
+  const float4* vh = (const float4*)c->vals_hi;
+  const float4* vl = (const float4*)c->vals_lo;
   if (prec == LB_FP32)
     k_epib<RC, PASS2, 1><<<eb, 256, 0, c->stream>>>(N, c->np, R, nsplit, part, c->nrm, c->row_ptr, c->near_patch,
-                                                     c->vals_hi, nullptr, D, o0, o1, o2, o3);
+                                                     vh, nullptr, D, o0, o1, o2, o3);
   else
     k_epib<RC, PASS2, 2><<<eb, 256, 0, c->stream>>>(N, c->np, R, nsplit, part, c->nrm, c->row_ptr, c->near_patch,
-                                                     c->vals_hi, c->vals_lo, D, o0, o1, o2, o3);
+                                                     vh, vl, D, o0, o1, o2, o3);
   LB_LAUNCH(c);
   return LB_OK;
 }
@@ -765,5 +742,6 @@ extern "C" int lb_get_tuning(lb_ctx* c, int* shapes) {
         auto it = g_tune.find(key);
         shapes[p * 4 + k * 2 + r] = it == g_tune.end() ? -1 : it->second;
       }
+  for (int kind = 0; kind < 4; ++kind) shapes[8 + kind] = lb_far_tuned_variant(c, kind);
   return LB_OK;
 }

@@ -55,15 +55,17 @@ __device__ __forceinline__ void df_pair(const float* t, const float4& A, const f
   }
   const F2 nxx = {t[6], t[9]}, nxy = {t[7], t[10]}, nxz = {t[8], t[11]};
   const F2 nxd = df_dot3(nxx, nxy, nxz, dx, dy, dz);
-  const F2 ex = df_sub(nxx, nyx), ey = df_sub(nxy, nyy), ez = df_sub(nxz, nyz);
-  const F2 dnd = df_dot3(ex, ey, ez, dx, dy, dz);
-  const F2 dn2 = df_dot3(ex, ey, ez, ex, ey, ez);
+  const F2 nyd = df_dot3(nyx, nyy, nyz, dx, dy, dz);
+  // (n_x - n_y).d = n_x.d - n_y.d, and for unit normals |n_x - n_y|^2 / 2 =
+  // 1 - n_x.n_y (double-float keeps its absolute error near 1e-16)
+  const F2 dnd = df_sub(nxd, nyd);
+  const F2 hdn2 = df_sub({1.f, 0.f}, df_dot3(nxx, nxy, nxz, nyx, nyy, nyz));
   // 3 (n_x.d)((n_x - n_y).d) / r^2 - |n_x - n_y|^2 / 2
-  const F2 kk = df_sub(df_scale(df_mul(df_mul(nxd, dnd), rinv2), 3.f), df_scale(dn2, 0.5f));
+  const F2 kk = df_sub(df_scale(df_mul(df_mul(nxd, dnd), rinv2), 3.f), hdn2);
   if (KIND == FAR_KALL) {
     const F2 qr3 = df_mul(q1, rinv3);
     df_acc(acc[0], df_mul(q1, rinv));
-    df_acc(acc[1], df_mul(qr3, df_dot3(nyx, nyy, nyz, dx, dy, dz)));
+    df_acc(acc[1], df_mul(qr3, nyd));
     df_acc(acc[2], df_mul(qr3, nxd));
     df_acc(acc[3], df_mul(qr3, kk));
   } else {  // FAR_K2: q1 = mu1, q2 = mu2
@@ -224,10 +226,9 @@ static int launch_df_t(lb_ctx* c, const void* S, double* part, int* nsplit_out) 
   MaskTable* m = nullptr;
   LB_CHECK(lb_get_mask_src(c, tb, TS, snp, spad, &m));
   const int64_t ntb = m->ntb, ntiles = m->ntiles;
-  const int64_t want = 6LL * c->sm_count;
-  int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(ntiles, (want + ntb - 1) / ntb));
+  int nsplit = 1;
+  LB_CHECK(lb_pick_nsplit(c, k_far_df<KIND, NT, NTH, TS>, NTH, ntb, ntiles, &nsplit));
   const int tps = (int)((ntiles + nsplit - 1) / nsplit);
-  nsplit = (ntiles + tps - 1) / tps;
   dim3 grid((unsigned)ntb, (unsigned)nsplit);
   ProfScope prof(c, LB_PROF_FARDF_K1 + KIND, pairs);
   k_far_df<KIND, NT, NTH, TS><<<grid, NTH, 0, c->stream>>>(c->N, snp, (const float4*)S, m->flags, ntiles,

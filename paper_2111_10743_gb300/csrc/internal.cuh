@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <map>
@@ -91,8 +92,9 @@ struct lb_ctx {
   int64_t* row_ptr = nullptr;   // [N+1]
   int32_t* near_patch = nullptr;  // [nnzb]
   double* vals = nullptr;       // [nnzb][4][np]
-  float* vals_hi = nullptr;     // [nnzb][4][np] float32 copy (double-float hi part), made on first use
-  float* vals_lo = nullptr;     // [nnzb][4][np] double-float lo part
+  float* vals_hi = nullptr;     // [nnzb][4][npp] float32 copy (double-float hi part), npp = lb_np_pad(np),
+                                // zero past np; made on first use
+  float* vals_lo = nullptr;     // [nnzb][4][npp] double-float lo part
   std::vector<MaskTable> masks;
   // transposed near structure (adjoint applies), built on first use
   bool have_trans = false;
@@ -254,6 +256,8 @@ int lb_pack_df(lb_ctx* c, const double* d1, const double* d2, void* S);
 int lb_pack_df_points(lb_ctx* c, int64_t n, int64_t npad, const double* Y, const double* nY, const double* wY,
                       const double* d1, const double* d2, void* S);
 int lb_far_launch_df(lb_ctx* c, int kind, const void* S, double* part, int* nsplit);
+// launch variant chosen for single-density float32 passes of `kind`, -1 if not tuned yet
+int lb_far_tuned_variant(lb_ctx* c, int kind);
 // A3 applied to R densities tau[R][N] -> out[R][N] with several densities per
 // far-field pass (prec LB_FP32 or LB_DF64); u (may be null) receives S[S[tau]]
 int lb_apply_a3_batch(lb_ctx* c, int prec, int R, const double* tau, double* out, double* u);
@@ -267,3 +271,42 @@ extern thread_local int lb_apply64_counter, lb_apply32_counter;
 extern thread_local int lb_graph_counter;  // GMRES iterations run as graph replays
 
 static inline unsigned lb_div_up(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+// Source-split count for a pair kernel launched as ntb target blocks x
+// nsplit source ranges of ntiles tiles: the smallest split (at most 32) whose
+// grid fills whole waves of the kernel's resident blocks to >= 97%, else the
+// best fill found.  The resident-block count is queried once per kernel, so
+// the launches of a captured iteration make no queries.
+template <typename F>
+int lb_pick_nsplit(lb_ctx* c, F kernel, int nth, int64_t ntb, int64_t ntiles, int* out) {
+  int per_sm = 0;
+  auto it = c->occupancy.find((const void*)kernel);
+  if (it != c->occupancy.end()) {
+    per_sm = it->second;
+  } else {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, nth, 0);
+    if (e != cudaSuccess) return lb_fail(c, LB_ECUDA, "occupancy query failed: %s", cudaGetErrorString(e));
+    c->occupancy[(const void*)kernel] = per_sm;
+  }
+  const int64_t slots = (int64_t)(per_sm > 0 ? per_sm : 1) * c->sm_count;
+  int best = 1;
+  double best_eff = -1;
+  const int64_t hi = ntiles < 32 ? ntiles : 32;
+  for (int64_t s = 1; s <= hi; ++s) {
+    const int64_t tps = (ntiles + s - 1) / s;
+    const int64_t ns = (ntiles + tps - 1) / tps;
+    const int64_t blocks = ntb * ns;
+    const double waves = (double)blocks / (double)slots;
+    const double eff = waves / std::ceil(waves);
+    if (eff > best_eff + 0.02) {
+      best_eff = eff;
+      best = (int)ns;
+    }
+    if (eff > 0.97 && blocks >= slots) break;
+  }
+  *out = best;
+  return LB_OK;
+}
+
+// nodes per patch rounded up to a multiple of four: row length of the float
+// copies of the correction weights and densities (16-byte loads)
+static inline int lb_np_pad(int np) { return (np + 3) & ~3; }
