@@ -377,6 +377,111 @@ def run_ours(args):
     print(json.dumps(out))
 
 
+def run_genus5(args):
+    """Configuration 5 with direct far-field sums: the genus-5 surface (five
+    blended tori, 36,272 order-6 patches, N = 1,015,616).  Corrections built
+    on the GPU; the harmonic fields of six seeded tangential F (12 Hodge
+    right-hand sides, the five of the configuration and one more so that the
+    rank gap after 2g = 10 can show) and four of its random f, solved in
+    lockstep with float32 pairs refined to 1e-9; the harmonic space's rank;
+    far sums against the FP64 oracle on 2,048 sampled targets.  The octree FMM
+    that the paper uses at this size is not built: every pass is a direct sum
+    over N^2 pairs, and the timings say what that costs."""
+    import torch
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    import paper_2111_10743_gb300 as lb
+    from oracle import farsum
+    from oracle.geometry import build_geometry, near_lists
+    from workloads import rhs as R
+    from workloads.configs import _centred, _tangential, config
+    t0 = time.time()
+    w = config(5)
+    s = w.surface
+    Xc, L = _centred(s)
+    F = np.concatenate([w.extra["F"],
+                        _tangential(s, R.legendre_field(Xc, np.random.default_rng(1105), 4, L, ncomp=3))[None]])
+    t_mesh = time.time() - t0
+    stream = torch.cuda.current_stream()
+    params = lb.default_params(eps_quad=1e-12, tol=w.tol, precision=lb.LB_FP32_REFINED, formulation=lb.LB_A3)
+    ctx = lb.Context(local, params, stream=stream)
+    ctx.upload_surface(s)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ctx.build_corrections()
+    torch.cuda.synchronize()
+    t_q = time.time() - t0
+    Fd = torch.tensor(F, device="cuda")
+    H = torch.empty((2 * F.shape[0],) + F.shape[1:], dtype=torch.float64, device="cuda")
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    _, info_h = ctx.harmonic_fields(Fd, out=H)
+    e[1].record(stream)
+    f = torch.tensor(w.f[:4], device="cuda")
+    u = torch.empty_like(f)
+    e[2].record(stream)
+    _, info_f = ctx.solve_lb(f, out=u)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    ms_h, ms_f = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    n, wq, _ = ctx.get_geometry()
+    Hh = H.cpu().numpy()
+    M = (Hh * np.sqrt(wq)[None, :, None]).reshape(Hh.shape[0], -1)
+    sv = np.sqrt(np.maximum(np.linalg.eigvalsh(M @ M.T)[::-1], 0.0))
+    div = ctx.surface_div(Hh)
+    divrel = max(float(np.sqrt(np.sum(wq * div[k] ** 2) / np.sum(wq * np.sum(Hh[k] ** 2, 1))))
+                 for k in range(Hh.shape[0]))
+    # far sums against the oracle on sampled targets (its own geometry and near lists)
+    geo = build_geometry(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv)
+    rng = np.random.default_rng(7)
+    targets = np.sort(rng.choice(s.N, 2048, replace=False)).astype(np.int64)
+    ptr, pl = near_lists_sampled(geo, targets, 2.0)
+    sig = rng.standard_normal(s.N)
+    ref = farsum.far_sums(geo, ptr, pl, sig, targets)[0]
+    errs = {}
+    for name, prec in (("fp32", lb.LB_FP32), ("df64", lb.LB_DF64)):
+        got = ctx.far_sums(sig[None], precision=prec)[0][:, targets]
+        errs[name] = max(float(np.abs(got[k] - ref[k]).max() / np.abs(ref[k]).max()) for k in range(4))
+    pairs = info_h["pairs"] + info_f["pairs"]
+    ctx.close()
+    print(json.dumps({
+        "metric": METRIC, "value": round(pairs / ((ms_h + ms_f) * 1e-3) / 1e9, 3), "unit": UNIT,
+        "case": "genus5", "data": "synthetic", "dtype": "f32 + double-float pairs, f64 solve",
+        "config": {"workload": f"genus-5 surface (5 blended tori), {s.npatch} order-6 patches (N={s.N:,}); "
+                               f"12 Hodge RHS (6 tangential F) + 4 Legendre f; A3 lockstep solves to 1e-9",
+                   "N": s.N, "patches": s.npatch, "order": s.order, "far_field": "direct sums (no FMM)"},
+        "mesh_s": round(t_mesh, 1), "t_q_s": round(t_q, 1),
+        "hodge": {"nrhs": 2 * F.shape[0], "ms": round(ms_h, 1), "iterations": info_h["iterations"],
+                  "refinements": info_h["refinements"], "rel_residual": info_h["rel_residual"],
+                  "converged": info_h["converged"]},
+        "random_f": {"nrhs": 4, "ms": round(ms_f, 1), "iterations": info_f["iterations"],
+                     "refinements": info_f["refinements"], "rel_residual": info_f["rel_residual"],
+                     "converged": info_f["converged"]},
+        "harmonic_space": {"fields": int(Hh.shape[0]), "sv_rel": [float(x / sv[0]) for x in sv],
+                           "rank_2g": int(np.sum(sv > 1e-3 * sv[0])), "max_rel_div": divrel},
+        "oracle_sampled_far_sums": {"targets": 2048, "max_rel_err": errs},
+        "pairs": int(pairs),
+    }))
+
+
+def near_lists_sampled(geo, targets, eta):
+    """Near lists by the oracle's rule for the sampled targets only, as a CSR
+    over all N rows (rows outside the sample are empty)."""
+    N = geo.N
+    counts = np.zeros(N, dtype=np.int64)
+    rows = []
+    for i in targets:
+        d = np.linalg.norm(geo.centroid - geo.X[i][None, :], axis=1)
+        r = np.nonzero(d < eta * geo.radius)[0].astype(np.int32)
+        rows.append(r)
+        counts[i] = len(r)
+    ptr = np.zeros(N + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum(counts)
+    return ptr, (np.concatenate(rows) if rows else np.zeros(0, dtype=np.int32))
+
+
 def torus_batch_record(lb, torch, device, stream, flush, steps=3, warmup=3):
     """The batched form on the torus R = 2, r = 0.75 (2,048 order-6 patches,
     N = 57,344): 16 random Legendre f and the two Hodge right-hand sides
@@ -581,10 +686,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain float64 solve after the timed region")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched torus record of the default line")
-    ap.add_argument("--case", default="full", choices=["full", "small", "torus_batch", "torus_small"],
+    ap.add_argument("--case", default="full", choices=["full", "small", "torus_batch", "torus_small", "genus5"],
                     help="full: the benchmark surface; small: 320 patches of the same kind (profiling); "
                          "torus_batch: the torus with 18 right-hand sides solved in lockstep; "
-                         "torus_small: the same batch on a 16 x 16 torus (profiling)")
+                         "torus_small: the same batch on a 16 x 16 torus (profiling); genus5: configuration 5 "
+                         "(N = 1,015,616) with direct far sums, one run")
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -600,6 +706,8 @@ def main():
         print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE {ws}; timing {ws} replica(s)", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.case == "genus5":
+        run_genus5(args)
     else:
         run_ours(args)
 

@@ -354,9 +354,11 @@ int lb_geometry_gradient(lb_ctx* ctx, int nrhs, const double* f, const double* g
  * 1: 8 densities per pass).  Values: 0 = 128 threads x 64-source tiles,
  * 1 = 128 x 128, 2 = 256 x 64, -1 = not tuned yet.  shapes[8 + kind], kind
  * 0..3 = K1 (S, grad S), all four kernels, A3 pass 2, A2 pass 2: the
- * variant chosen by timing for single-density float32 passes (K1: 0 scalar,
- * 1 two sources per packed instruction; the others: 0 packed, 1 packed with
- * registers capped for three resident blocks per SM), -1 = not tuned yet.
+ * variant chosen by timing for single-density float32 passes (K1: 0 scalar
+ * with 4 targets per thread, 1 two sources per packed instruction, 2 scalar
+ * with 8 targets per thread; the others: 0 packed with 4 targets per thread,
+ * 1 the same with registers capped for three resident blocks per SM, 2
+ * packed with 2 targets per thread), -1 = not tuned yet.
  * shapes: host memory of 12 ints. */
 int lb_get_tuning(lb_ctx* ctx, int* shapes);
 

@@ -221,8 +221,8 @@ class Context:
             for k, kn in enumerate(("k1", "k2")):
                 for r, rn in enumerate(("rc4", "rc8")):
                     out[f"{pn}_{kn}_{rn}"] = names[a[p * 4 + k * 2 + r]]
-        single = {0: ("scalar", "packed"), 1: ("packed", "packed_3blocks"), 2: ("packed", "packed_3blocks"),
-                  3: ("packed", "packed_3blocks")}
+        pk = ("packed_nt4", "packed_nt4_3blocks", "packed_nt2")
+        single = {0: ("scalar_nt4", "packed_nt4", "scalar_nt8"), 1: pk, 2: pk, 3: pk}
         for kind, kn in enumerate(("k1", "kall", "k2", "k4")):
             v = a[8 + kind]
             out[f"far32_single_{kn}"] = single[kind][v] if v >= 0 else None

@@ -498,24 +498,32 @@ static int launch_far32x2(lb_ctx* c, const void* srcA, const void* srcB, double*
   return LB_OK;
 }
 
-// Single-density float32 passes: two launch variants per kind, chosen by
-// timing.  K1: the scalar kernel (variant 0) or the packed two-source kernel
-// (1); the longer kinds: the packed kernel at its natural register count (0)
-// or capped for three resident blocks per SM (1).
+// Single-density float32 passes: three launch variants per kind, chosen by
+// timing.  K1: the scalar kernel with 4 targets per thread (variant 0), the
+// packed two-source kernel capped for three resident blocks per SM (1), the
+// scalar kernel with 8 targets per thread
+// (2); the longer kinds: the packed kernel with 4 targets per thread at its
+// natural register count (0), capped for three resident blocks per SM (1),
+// with 2 targets per thread (2).
+#define LB_FP32_VARIANTS 3
 static int launch_fp32(lb_ctx* c, int kind, int variant, const void* A, const void* B, double* part, int* ns) {
   switch (kind) {
     case FAR_K1:
-      return variant ? launch_far32x2<FAR_K1, 4, 128, 128>(c, A, B, part, ns)
-                     : launch_far_t<float, FAR_K1, 4, 128, 128>(c, A, B, part, ns);
+      if (variant == 1) return launch_far32x2<FAR_K1, 4, 128, 128, 3>(c, A, B, part, ns);
+      if (variant == 2) return launch_far_t<float, FAR_K1, 8, 128, 128>(c, A, B, part, ns);
+      return launch_far_t<float, FAR_K1, 4, 128, 128>(c, A, B, part, ns);
     case FAR_KALL:
-      return variant ? launch_far32x2<FAR_KALL, 4, 128, 128, 3>(c, A, B, part, ns)
-                     : launch_far32x2<FAR_KALL, 4, 128, 128>(c, A, B, part, ns);
+      if (variant == 1) return launch_far32x2<FAR_KALL, 4, 128, 128, 3>(c, A, B, part, ns);
+      if (variant == 2) return launch_far32x2<FAR_KALL, 2, 128, 128>(c, A, B, part, ns);
+      return launch_far32x2<FAR_KALL, 4, 128, 128>(c, A, B, part, ns);
     case FAR_K2:
-      return variant ? launch_far32x2<FAR_K2, 4, 128, 128, 3>(c, A, B, part, ns)
-                     : launch_far32x2<FAR_K2, 4, 128, 128>(c, A, B, part, ns);
+      if (variant == 1) return launch_far32x2<FAR_K2, 4, 128, 128, 3>(c, A, B, part, ns);
+      if (variant == 2) return launch_far32x2<FAR_K2, 2, 128, 128>(c, A, B, part, ns);
+      return launch_far32x2<FAR_K2, 4, 128, 128>(c, A, B, part, ns);
     default:
-      return variant ? launch_far32x2<FAR_K4, 4, 128, 128, 3>(c, A, B, part, ns)
-                     : launch_far32x2<FAR_K4, 4, 128, 128>(c, A, B, part, ns);
+      if (variant == 1) return launch_far32x2<FAR_K4, 4, 128, 128, 3>(c, A, B, part, ns);
+      if (variant == 2) return launch_far32x2<FAR_K4, 2, 128, 128>(c, A, B, part, ns);
+      return launch_far32x2<FAR_K4, 4, 128, 128>(c, A, B, part, ns);
   }
 }
 
@@ -554,7 +562,7 @@ static int fp32_variant(lb_ctx* c, int kind, const void* A, const void* B, doubl
     rc = lb_fail(c, LB_ECUDA, "cudaEventCreate failed");
   float best_ms = 1e30f;
   int best = 0;
-  for (int v = 0; v < 2 && rc == LB_OK; ++v) {
+  for (int v = 0; v < LB_FP32_VARIANTS && rc == LB_OK; ++v) {
     int ns = 0;
     rc = launch_fp32(c, kind, v, A, B, part, &ns);  // warm-up (module load, occupancy query)
     if (rc == LB_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = lb_fail(c, LB_ECUDA, "event record");
@@ -776,7 +784,8 @@ __global__ void k_epilogue(int64_t N, int np, int npv, int nsplit, int nacc, con
   }
   // split partials of output o summed by lanes 8 o .. 8 o + 7, eight splits
   // apart (float64 for float64 passes, else (hi, lo) float pairs summed in
-  // double-float arithmetic), then combined by three shuffles
+  // double-float arithmetic), then combined by three shuffles; nsplit < 0:
+  // a single float64 sum per accumulator (the symmetric double-float kernels)
   const int o = lane >> 3, sub = lane & 7;
   const int oo = o < sp.nout ? o : 0;
   const int a0 = sp.acc[oo];
@@ -786,18 +795,33 @@ __global__ void k_epilogue(int64_t N, int np, int npv, int nsplit, int nacc, con
   for (int k = 0; k < 3; ++k) g[k] = P{};
   const int na = a0 >= 0 ? 1 : 3;
   const int ab = a0 >= 0 ? a0 : 1;
-  for (int s = sub; s < nsplit; s += 8)
+  if (nsplit < 0) {  // one float64 sum per accumulator, [nacc][N]
+    if (sub == 0)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (k >= na) break;
-      const int64_t idx = ((int64_t)s * nacc + ab + k) * N + i;
-      if constexpr (MODE == 0) {
-        g[k] += part[idx];
-      } else {
-        const float2 v = reinterpret_cast<const float2*>(part)[idx];
-        g[k] = df_add(g[k], {v.x, v.y});
+      for (int k = 0; k < 3; ++k) {
+        if (k >= na) break;
+        const double v = part[(int64_t)(ab + k) * N + i];
+        if constexpr (MODE == 0) {
+          g[k] = v;
+        } else {
+          const float h = (float)v;
+          g[k] = {h, (float)(v - (double)h)};
+        }
       }
-    }
+  } else {
+    for (int s = sub; s < nsplit; s += 8)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (k >= na) break;
+        const int64_t idx = ((int64_t)s * nacc + ab + k) * N + i;
+        if constexpr (MODE == 0) {
+          g[k] += part[idx];
+        } else {
+          const float2 v = reinterpret_cast<const float2*>(part)[idx];
+          g[k] = df_add(g[k], {v.x, v.y});
+        }
+      }
+  }
 #pragma unroll
   for (int off = 4; off > 0; off >>= 1)
 #pragma unroll

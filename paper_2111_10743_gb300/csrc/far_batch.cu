@@ -210,9 +210,10 @@ __global__ void __maxnreg__(200) k_farbdf(int64_t N, int64_t Npad, int np, const
         near_bits(flags[(int64_t)blockIdx.x * ntiles + tile] != 0, t, N, P0, row_ptr, near_patch);
     for (int s = 0; s < TS; ++s) {
       const float4 A = sA[s], B = sB[s];
-      const F2 dx = {ta.x - A.x, tb.x - B.x};
-      const F2 dy = {ta.y - A.y, tb.y - B.y};
-      const F2 dz = {ta.z - A.z, tb.z - B.z};
+      // exact renormalisation of the grid-split difference (as in far_df.cu)
+      const F2 dx = fast_two_sum(ta.x - A.x, tb.x - B.x);
+      const F2 dy = fast_two_sum(ta.y - A.y, tb.y - B.y);
+      const F2 dz = fast_two_sum(ta.z - A.z, tb.z - B.z);
       F2 rinv = df_rsqrt(df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz)));
       if ((m >> sLp[s]) & 1ull) rinv = {0.f, 0.f};
       const F2 rinv2 = df_sqr(rinv);

@@ -28,10 +28,15 @@ template <> struct DfOut<FAR_K4> { static const int n = 2; };
 template <int KIND>
 __device__ __forceinline__ void df_pair(const float* t, const float4& A, const float4& B, const float4& C,
                                         const float4& D, bool masked, F2* acc) {
-  // t: x_hi[3], x_lo[3], n_hi[3], n_lo[3] of the target
-  const F2 dx = {t[0] - A.x, t[3] - B.x};
-  const F2 dy = {t[1] - A.y, t[4] - B.y};
-  const F2 dz = {t[2] - A.z, t[5] - B.z};
+  // t: x_hi[3], x_lo[3], n_hi[3], n_lo[3] of the target.  The grid
+  // difference is exact and either zero or at least h, the lo difference at
+  // most h, so FastTwoSum renormalises d exactly; without it |lo| / |hi| can
+  // reach h / r (2e-5 for close pairs on a large surface), and the products
+  // below, which drop lo * lo and round hi * lo to float, would lose that
+  // ratio squared.
+  const F2 dx = fast_two_sum(t[0] - A.x, t[3] - B.x);
+  const F2 dy = fast_two_sum(t[1] - A.y, t[4] - B.y);
+  const F2 dz = fast_two_sum(t[2] - A.z, t[5] - B.z);
   const F2 r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
   F2 rinv = df_rsqrt(r2);
   if (masked) rinv = {0.f, 0.f};
@@ -239,7 +244,200 @@ static int launch_df_t(lb_ctx* c, const void* S, double* part, int* nsplit_out) 
   return LB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric pair sums (node sources, passes K1 and K2).  The kernels are
+// functions of d = x_i - y_j, r and the two normals, so one evaluation of an
+// unordered pair {i, j} serves both directions: d, r, 1/r, 1/r^3, n_i.d,
+// n_j.d and 1 - n_i.n_j are shared, and only the charges and the signs of
+// the odd terms differ (for target j: d -> -d, so n_j.d' = -n_j.d and
+// (n_j - n_i).d' = (n_i - n_j).d).  Each CTA takes one pair of node blocks
+// (I, J), I <= J, B nodes each: thread t holds target i = I B + t and loops
+// over the sources j of block J, accumulating its own (i-side) sums in
+// registers and the j-side sums of GS sources at a time, which a warp
+// reduce-scatter (31 shuffles per 32 lanes) and a sum over the CTA's warps
+// turn into one value per source.  Diagonal blocks (I = J) take the i-side
+// only, so every ordered pair is evaluated exactly once.  The near mask
+// holds per direction (Near is not symmetric): bit patch(j) of Near(i) for
+// the i-side, bit patch(i) of Near(j), gathered per source into shared
+// memory, for the j-side.  Sums leave each CTA as float64 additions to
+// out[4][N] (red.global.add.f64): the order of those additions, and so the
+// last bit of the result, is not fixed from run to run.
+template <int KIND>
+__device__ __forceinline__ void df_pair_sym(const float* t, const float4& A, const float4& B, const float4& C,
+                                            const float4& D, bool mi, bool mj, F2* acci, F2* accj) {
+  // t: x_hi[3], x_lo[3], n_hi[3], n_lo[3], q1 (hi, lo), q2 (hi, lo) of the target
+  const F2 dx = fast_two_sum(t[0] - A.x, t[3] - B.x);
+  const F2 dy = fast_two_sum(t[1] - A.y, t[4] - B.y);
+  const F2 dz = fast_two_sum(t[2] - A.z, t[5] - B.z);
+  const F2 r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+  F2 rinv = df_rsqrt(r2);
+  if (mi && mj) rinv = {0.f, 0.f};  // both directions masked (the self pair, padding)
+  const F2 zero = {0.f, 0.f};
+  const F2 q1j = mi ? zero : F2{A.w, B.w};    // source charges, i-side
+  const F2 q1i = mj ? zero : F2{t[12], t[13]};  // target charges, j-side
+  const F2 rinv2 = df_sqr(rinv);
+  const F2 rinv3 = df_mul(rinv2, rinv);
+  if (KIND == FAR_K1) {
+    // S: q / r; gradient sums: q d / r^3 (d' = -d for the j-side)
+    df_acc(acci[0], df_mul(q1j, rinv));
+    df_acc(accj[0], df_mul(q1i, rinv));
+    const F2 tj = df_mul(q1j, rinv3);
+    const F2 ti = df_mul(F2{-q1i.h, -q1i.l}, rinv3);
+    df_acc(acci[1], df_mul(tj, dx));
+    df_acc(acci[2], df_mul(tj, dy));
+    df_acc(acci[3], df_mul(tj, dz));
+    df_acc(accj[1], df_mul(ti, dx));
+    df_acc(accj[2], df_mul(ti, dy));
+    df_acc(accj[3], df_mul(ti, dz));
+    return;
+  }
+  // FAR_K2: q1 = mu1, q2 = mu2
+  const F2 q2j = mi ? zero : F2{C.w, D.w};
+  const F2 q2i = mj ? zero : F2{t[14], t[15]};
+  const F2 nxx = {t[6], t[9]}, nxy = {t[7], t[10]}, nxz = {t[8], t[11]};
+  const F2 nyx = {C.x, D.x}, nyy = {C.y, D.y}, nyz = {C.z, D.z};
+  const F2 a = df_dot3(nxx, nxy, nxz, dx, dy, dz);  // n_i.d
+  const F2 b = df_dot3(nyx, nyy, nyz, dx, dy, dz);  // n_j.d
+  const F2 cc = df_sub(a, b);                       // (n_i - n_j).d
+  const F2 hdn2 = df_sub({1.f, 0.f}, df_dot3(nxx, nxy, nxz, nyx, nyy, nyz));
+  const F2 c3 = df_scale(df_mul(cc, rinv2), 3.f);   // 3 (n_i - n_j).d / r^2
+  // i-side: K = 3 a c / r^2 - (1 - n_i.n_j); j-side: -(3 b c / r^2 + 1 - n_i.n_j)
+  const F2 kki = df_sub(df_mul(a, c3), hdn2);
+  const F2 kkj = df_add(df_mul(b, c3), hdn2);
+  const F2 tti = df_mul(a, rinv3);
+  const F2 ttj = df_mul(F2{-b.h, -b.l}, rinv3);
+  df_acc(acci[0], df_mul(q1j, tti));
+  df_acc(acci[1], df_mul(q2j, rinv));
+  df_acc(acci[2], df_mul(q2j, tti));
+  df_acc(acci[3], df_mul(df_mul(q2j, rinv3), kki));
+  df_acc(accj[0], df_mul(q1i, ttj));
+  df_acc(accj[1], df_mul(q2i, rinv));
+  df_acc(accj[2], df_mul(q2i, ttj));
+  df_acc(accj[3], df_mul(df_mul(F2{-q2i.h, -q2i.l}, rinv3), kkj));
+}
+
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+template <int KIND, int B, int GS>
+__global__ void __launch_bounds__(B) k_far_df_sym(int64_t N, int np, int nb, const float4* __restrict__ S,
+                                                  int64_t Npad, const uint8_t* __restrict__ flags, int64_t ntiles,
+                                                  const int64_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ near_patch, double* __restrict__ out) {
+  constexpr int NO = 4, NW = B / 32;
+  static_assert(GS * NO <= 32 && (GS * NO & (GS * NO - 1)) == 0, "reduce-scatter width");
+  __shared__ float4 sA[B], sB[B], sC[B], sD[B];
+  __shared__ unsigned long long sMask[B];
+  __shared__ int sLp[B];
+  __shared__ F2 sRed[NW][B][NO];
+  // block pair (I, J), I <= J, from the linear index J (J + 1) / 2 + I
+  const int64_t lin = blockIdx.x;
+  int64_t J = (int64_t)((sqrt(8.0 * (double)lin + 1.0) - 1.0) * 0.5);
+  while (J * (J + 1) / 2 > lin) --J;
+  while ((J + 1) * (J + 2) / 2 <= lin) ++J;
+  const int64_t I = lin - J * (J + 1) / 2;
+  const bool diag = I == J;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t i = I * B + tid, j = J * B + tid;
+  const int64_t P0I = (I * B) / np, P0J = (J * B) / np;
+  const bool any = flags[I * ntiles + J] != 0 || flags[J * ntiles + I] != 0;
+  // stage block J and the j-side masks; load the target
+  sA[tid] = S[j];
+  sB[tid] = S[Npad + j];
+  sC[tid] = S[2 * Npad + j];
+  sD[tid] = S[3 * Npad + j];
+  sLp[tid] = (int)(j / np - P0J);
+  unsigned long long mj = 0ull;
+  if (any && !diag && j < N)
+    for (int64_t bb = row_ptr[j]; bb < row_ptr[j + 1]; ++bb) {
+      const int64_t d = (int64_t)near_patch[bb] - P0I;
+      if (d >= 0 && d < 64) mj |= 1ull << d;
+    }
+  sMask[tid] = mj;
+  unsigned long long mi = 0ull;
+  if (any && i < N)
+    for (int64_t bb = row_ptr[i]; bb < row_ptr[i + 1]; ++bb) {
+      const int64_t d = (int64_t)near_patch[bb] - P0J;
+      if (d >= 0 && d < 64) mi |= 1ull << d;
+    }
+  const int lpi = (int)(i / np - P0I);
+  const bool pad_i = i >= N;
+  float tv[16];
+  {
+    const float4 a = S[i], b = S[Npad + i], c = S[2 * Npad + i], d = S[3 * Npad + i];
+    tv[0] = a.x; tv[1] = a.y; tv[2] = a.z;
+    tv[3] = b.x; tv[4] = b.y; tv[5] = b.z;
+    tv[6] = c.x; tv[7] = c.y; tv[8] = c.z;
+    tv[9] = d.x; tv[10] = d.y; tv[11] = d.z;
+    tv[12] = a.w; tv[13] = b.w; tv[14] = c.w; tv[15] = d.w;
+  }
+  F2 acci[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) acci[o] = {0.f, 0.f};
+  __syncthreads();
+  for (int g = 0; g < B; g += GS) {
+    F2 accj[GS * NO];
+#pragma unroll
+    for (int k = 0; k < GS * NO; ++k) accj[k] = {0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < GS; ++u) {
+      const int s = g + u;
+      const bool msk_i = pad_i || ((mi >> sLp[s]) & 1ull);
+      const bool msk_j = diag || pad_i || ((sMask[s] >> lpi) & 1ull);
+      df_pair_sym<KIND>(tv, sA[s], sB[s], sC[s], sD[s], msk_i, msk_j, acci, accj + u * NO);
+    }
+    if (!diag) {
+      warp_reduce_scatter<GS * NO>(accj, lane);
+      // value k = u NO + o ends in lanes k << (5 - log2(GS NO)) and up
+      constexpr int SH = 5 - Log2<GS * NO>::value;
+      if ((lane & ((1 << SH) - 1)) == 0) {
+        const int k = lane >> SH;
+        sRed[warp][g + k / NO][k % NO] = accj[0];
+      }
+    }
+  }
+  if (!pad_i)
+#pragma unroll
+    for (int o = 0; o < NO; ++o) red_add_f64(out + o * N + i, df_to_double(acci[o]));
+  if (diag) return;
+  __syncthreads();
+  if (j < N)
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      F2 v = sRed[0][tid][o];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) v = df_add(v, sRed[w][tid][o]);
+      red_add_f64(out + o * N + j, df_to_double(v));
+    }
+}
+
+template <int KIND>
+static int launch_df_sym(lb_ctx* c, const void* S, double* part) {
+  constexpr int B = 128, GS = 4;
+  if (c->np * 62 < B) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
+  if (c->Npad % B) return lb_fail(c, LB_EINVAL, "node padding is not a multiple of the block");
+  MaskTable* m = nullptr;
+  LB_CHECK(lb_get_mask_src(c, B, B, c->np, c->Npad, &m));
+  const int64_t nb = m->ntb;  // blocks holding nodes; the rest are padding
+  const int64_t nblk = nb * (nb + 1) / 2;
+  if (nblk > 0x7fffffffLL) return lb_fail(c, LB_EINVAL, "too many node blocks for one launch");
+  LB_CUDA(c, cudaMemsetAsync(part, 0, 4 * c->N * sizeof(double), c->stream));
+  const int64_t pairs = c->N * c->N;
+  ProfScope prof(c, LB_PROF_FARDF_K1 + KIND, pairs);
+  k_far_df_sym<KIND, B, GS><<<(unsigned)nblk, B, 0, c->stream>>>(c->N, c->np, (int)nb, (const float4*)S, c->Npad,
+                                                                  m->flags, m->ntiles, c->row_ptr, c->near_patch,
+                                                                  part);
+  LB_LAUNCH(c);
+  lb_pair_counter += pairs;
+  return LB_OK;
+}
+
 int lb_far_launch_df(lb_ctx* c, int kind, const void* S, double* part, int* nsplit) {
+  if ((kind == FAR_K1 || kind == FAR_K2) && !c->far_order) {
+    *nsplit = -1;
+    return kind == FAR_K1 ? launch_df_sym<FAR_K1>(c, S, part) : launch_df_sym<FAR_K2>(c, S, part);
+  }
   switch (kind) {
     case FAR_K1: return launch_df_t<FAR_K1>(c, S, part, nsplit);
     case FAR_KALL: return launch_df_t<FAR_KALL>(c, S, part, nsplit);

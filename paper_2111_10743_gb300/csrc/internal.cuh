@@ -255,6 +255,10 @@ int lb_split_f64(lb_ctx* c, int64_t n, const double* x, float* hi, float* lo);
 int lb_pack_df(lb_ctx* c, const double* d1, const double* d2, void* S);
 int lb_pack_df_points(lb_ctx* c, int64_t n, int64_t npad, const double* Y, const double* nY, const double* wY,
                       const double* d1, const double* d2, void* S);
+// Double-float pass of `kind` over the packed planes S.  *nsplit > 0: part
+// holds nsplit split partials [nsplit][4][N] of (hi, lo) float pairs;
+// *nsplit == -1: part holds one float64 sum per accumulator, [4][N] (the
+// symmetric kernel of the node-source passes K1 and K2).
 int lb_far_launch_df(lb_ctx* c, int kind, const void* S, double* part, int* nsplit);
 // launch variant chosen for single-density float32 passes of `kind`, -1 if not tuned yet
 int lb_far_tuned_variant(lb_ctx* c, int kind);

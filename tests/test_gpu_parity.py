@@ -100,6 +100,44 @@ def test_far_sums_fp64_fp32(lb, name):
         assert _rel(gotdf[:, k], ref[:, k]) < 5e-12, k
 
 
+def test_far_sums_df64_coarse_grid(lb):
+    """Double-float far sums when the position grid is coarse next to the
+    pair distances: two spheres of radius 0.05 twelve units apart (2 x 80
+    order-6 patches, N = 4,480).  The recentred coordinates reach 6, so the
+    grid step of the hi parts is 2^-20, and close far pairs are about 0.02
+    apart: the lo parts of the differences are up to 5e-5 of the hi parts.
+    Unless the differences are renormalised before they are squared, the
+    dropped lo * lo products alone put about 1e-9 into the closest terms;
+    with it the error is that of the 48-bit positions (2^-44 absolute)."""
+    from oracle import farsum
+    from oracle.geometry import build_geometry, near_lists
+    from workloads import surfaces as S
+    from workloads.surfaces import Surface
+    a = S.icosphere(1, 6)
+    parts = []
+    for c in ((-6.0, 0.3, 0.0), (6.0, 0.0, -0.2)):
+        parts.append((np.asarray(c) + 0.05 * a.X, 0.05 * a.Xu, 0.05 * a.Xv))
+    s = Surface("two_spheres", a.order, 2 * a.npatch, a.uv, a.wref, *(np.concatenate(z) for z in zip(*parts)))
+    g = build_geometry(s.order, s.uv, s.wref, s.X, s.Xu, s.Xv)
+    ptr, pl = near_lists(g, 2.0)
+    ctx = lb.Context(0, lb.default_params(eps_quad=1e-10, near_factor=2.0))
+    ctx.upload_surface(s)
+    ctx.build_near()
+    rp, pa, _ = ctx.get_corrections(with_vals=False)
+    assert np.array_equal(rp, ptr) and np.array_equal(pa, pl)
+    rng = np.random.default_rng(23)
+    sig = rng.standard_normal((2, s.N))
+    ref = farsum.far_sums(g, ptr, pl, sig)
+    gotdf = ctx.far_sums(sig, precision=lb.LB_DF64)
+    got64 = ctx.far_sums(sig, precision=lb.LB_FP64)
+    for k in range(4):
+        assert _rel(got64[:, k], ref[:, k]) < 1e-12, k
+        e = _rel(gotdf[:, k], ref[:, k])
+        print(f"kernel {k}: double-float {e:.2e}")
+        assert e < 2e-11, (k, e)
+    ctx.close()
+
+
 @pytest.mark.parametrize("name", CASES)
 def test_potentials_with_oracle_corrections(lb, name):
     ctx, s, d = ctx_for(lb, name)

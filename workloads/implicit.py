@@ -315,12 +315,18 @@ def mesh(surf, h: float, smooth: int = 8, relax: float = 0.5):
     else:
         raise ValueError(f"no manifold surface-nets mesh of spacing {h}")
     V = project(surf, V)
-    # split each quad along its shorter diagonal
+    # split each quad along its shorter diagonal.  Quads of surface nets are
+    # often symmetric, so the two lengths can agree to the last bit, and the
+    # last bits of the vertices depend on the host's exp; a near tie therefore
+    # takes the 0-2 diagonal (the 1-3 one only when shorter by a relative
+    # 1e-9, far above rounding), and quad q gives triangles 2 q and 2 q + 1,
+    # so that the mesh, its order included, is the same on every machine.
     d02 = np.linalg.norm(V[Q[:, 0]] - V[Q[:, 2]], axis=1)
     d13 = np.linalg.norm(V[Q[:, 1]] - V[Q[:, 3]], axis=1)
-    use02 = d02 <= d13
-    T = np.concatenate([Q[use02][:, [0, 1, 2]], Q[use02][:, [0, 2, 3]],
-                        Q[~use02][:, [0, 1, 3]], Q[~use02][:, [1, 2, 3]]])
+    use13 = (d13 < (1.0 - 1e-9) * d02)[:, None]
+    T = np.empty((2 * len(Q), 3), dtype=Q.dtype)
+    T[0::2] = np.where(use13, Q[:, [0, 1, 3]], Q[:, [0, 1, 2]])
+    T[1::2] = np.where(use13, Q[:, [1, 2, 3]], Q[:, [0, 2, 3]])
     nbr = _neighbours(T, len(V))
     deg = np.array([len(x) for x in nbr])
     rows = np.repeat(np.arange(len(V)), deg)
