@@ -358,7 +358,8 @@ int lb_geometry_gradient(lb_ctx* ctx, int nrhs, const double* f, const double* g
  * with 4 targets per thread, 1 two sources per packed instruction, 2 scalar
  * with 8 targets per thread; the others: 0 packed with 4 targets per thread,
  * 1 the same with registers capped for three resident blocks per SM, 2
- * packed with 2 targets per thread), -1 = not tuned yet.
+ * packed with 2 targets per thread; K1 and A3 pass 2 also 3: each unordered
+ * node pair evaluated once for both directions), -1 = not tuned yet.
  * shapes: host memory of 12 ints. */
 int lb_get_tuning(lb_ctx* ctx, int* shapes);
 
@@ -403,6 +404,14 @@ int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, const double* n
  * the next call that needs it, so the context stays usable; a failed
  * lb_upload_geometry leaves no geometry (upload again). */
 int lb_debug_fail_alloc(lb_ctx* ctx, int64_t after);
+
+/* Launch variant of the single-density float32 passes for tests (not in the
+ * paper): variant v (as reported in lb_get_tuning's shapes[8 + kind]) is
+ * used for pass `kind` (0..3) on this context's surface from now on, in this
+ * process, in place of the timed choice.  LB_EINVAL for a kind or variant out
+ * of range (variant 3 exists for kinds 0 and 2 only); LB_ESTATE before a
+ * geometry is uploaded. */
+int lb_debug_set_variant(lb_ctx* ctx, int kind, int variant);
 
 /* Surface divergence of tangential fields F [nrhs][N][3] -> out [nrhs][N]
  * (Section 2; host or device).  Used for the Hodge right-hand sides and to

@@ -107,6 +107,7 @@ def _load():
         "lb_fmm_plan_arrays": [P, P, P, P, P, P, P, P, P, P],
         "lb_fmm_plan_destroy": [P],
         "lb_debug_fail_alloc": [P, ctypes.c_int64],
+        "lb_debug_set_variant": [P, ctypes.c_int, ctypes.c_int],
         "lb_set_far_rule": [P, ctypes.c_int, P, P],
         "lb_geometry_gradient": [P, ctypes.c_int, P, P, P, P, P, P],
     }
@@ -208,6 +209,12 @@ class Context:
         of memory (test hook; after < 0 disarms)."""
         self._check(_lib.lb_debug_fail_alloc(self._h, int(after)))
 
+    def debug_set_variant(self, kind: int, variant: int):
+        """Use float32 launch variant `variant` for pass `kind` (0 K1, 1 all
+        four kernels, 2 A3 pass 2, 3 A2 pass 2) on this surface instead of
+        the timed choice (test hook)."""
+        self._check(_lib.lb_debug_set_variant(self._h, int(kind), int(variant)))
+
     def set_profiling(self, on: bool = True):
         self._check(_lib.lb_set_profiling(self._h, 1 if on else 0))
 
@@ -221,8 +228,8 @@ class Context:
             for k, kn in enumerate(("k1", "k2")):
                 for r, rn in enumerate(("rc4", "rc8")):
                     out[f"{pn}_{kn}_{rn}"] = names[a[p * 4 + k * 2 + r]]
-        pk = ("packed_nt4", "packed_nt4_3blocks", "packed_nt2")
-        single = {0: ("scalar_nt4", "packed_nt4", "scalar_nt8"), 1: pk, 2: pk, 3: pk}
+        pk = ("packed_nt4", "packed_nt4_3blocks", "packed_nt2", "symmetric")
+        single = {0: ("scalar_nt4", "packed_nt4", "scalar_nt8", "symmetric"), 1: pk, 2: pk, 3: pk}
         for kind, kn in enumerate(("k1", "kall", "k2", "k4")):
             v = a[8 + kind]
             out[f"far32_single_{kn}"] = single[kind][v] if v >= 0 else None

@@ -82,11 +82,28 @@ __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
   return r;
 }
 
+// float64 addition to global memory without a returned value (the symmetric
+// pair kernels' sums; the order of additions is not fixed)
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// block pair (I, J), I <= J, of the linear index lin = J (J + 1) / 2 + I
+__device__ __forceinline__ void tri_pair(int64_t lin, int64_t& I, int64_t& J) {
+  J = (int64_t)((sqrt(8.0 * (double)lin + 1.0) - 1.0) * 0.5);
+  while (J * (J + 1) / 2 > lin) --J;
+  while ((J + 1) * (J + 2) / 2 <= lin) ++J;
+  I = lin - J * (J + 1) / 2;
+}
+
 // ---- warp reductions --------------------------------------------------------
 __device__ __forceinline__ float shfl_xor_v(float v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
 __device__ __forceinline__ double shfl_xor_v(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
 __device__ __forceinline__ F2 shfl_xor_v(F2 v, int off) {
   return {__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)};
+}
+__device__ __forceinline__ F2 shfl_idx_v(F2 v, int src) {
+  return {__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src)};
 }
 __device__ __forceinline__ float add_v(float a, float b) { return a + b; }
 __device__ __forceinline__ double add_v(double a, double b) { return a + b; }

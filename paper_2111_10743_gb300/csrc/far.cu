@@ -407,6 +407,168 @@ __global__ void __launch_bounds__(NTH, MINB) k_far32x2(int64_t N, int np, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric float32 pair sums (A3 passes K1 and K2, node sources): each
+// unordered pair {i, j} evaluated once for both directions, in the layout of
+// the double-float kernel k_far_df_sym (far_df.cu): CTAs over block pairs
+// I <= J of 128 nodes, target sums in registers, source sums circulating one
+// lane per step through 32 x 32 warp tiles, float64 red.add of each CTA's
+// sums.  d, r, 1/r, 1/r^3, n_i.d, n_j.d and |n_i - n_j|^2 are shared; for
+// target j, d -> -d.  Block pairs without a near pair in either direction
+// take a loop without masks.
+template <int KIND, bool MASKED>
+__device__ __forceinline__ void f32_pair_sym(const float4& ta, const float4& tb, const float4& a, const float4& b,
+                                             bool mi, bool mj, float* acci, float* accj) {
+  // ta = (x_i, q1_i), tb = (n_i, q2_i); a = (y_j, q1_j), b = (n_j, q2_j)
+  const float dx = ta.x - a.x, dy = ta.y - a.y, dz = ta.z - a.z;
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  float rinv = lb_rsqrt(r2);
+  float q1j = a.w, q1i = ta.w;
+  if (MASKED) {
+    if (mi && mj) rinv = 0.f;
+    if (mi) q1j = 0.f;
+    if (mj) q1i = 0.f;
+  }
+  const float rinv3 = rinv * rinv * rinv;
+  if (KIND == FAR_K1) {
+    acci[0] = fmaf(q1j, rinv, acci[0]);
+    accj[0] = fmaf(q1i, rinv, accj[0]);
+    const float tj = q1j * rinv3, ti = q1i * rinv3;
+    acci[1] = fmaf(tj, dx, acci[1]);
+    acci[2] = fmaf(tj, dy, acci[2]);
+    acci[3] = fmaf(tj, dz, acci[3]);
+    accj[1] = fmaf(-ti, dx, accj[1]);
+    accj[2] = fmaf(-ti, dy, accj[2]);
+    accj[3] = fmaf(-ti, dz, accj[3]);
+    return;
+  }
+  float q2j = b.w, q2i = tb.w;
+  if (MASKED) {
+    if (mi) q2j = 0.f;
+    if (mj) q2i = 0.f;
+  }
+  const float an = fmaf(tb.z, dz, fmaf(tb.y, dy, tb.x * dx));  // n_i.d
+  const float ex = tb.x - b.x, ey = tb.y - b.y, ez = tb.z - b.z;
+  const float cn = fmaf(ez, dz, fmaf(ey, dy, ex * dx));          // (n_i - n_j).d
+  const float bn = an - cn;                                      // n_j.d
+  const float hd = 0.5f * fmaf(ez, ez, fmaf(ey, ey, ex * ex));  // 1 - n_i.n_j
+  const float c3 = cn * (3.f * rinv * rinv);
+  // target i: 3 a c / r^2 - hd; target j: -(3 b c / r^2 + hd)
+  const float kki = fmaf(an, c3, -hd), kkj = fmaf(bn, c3, hd);
+  const float tti = an * rinv3, ttj = bn * rinv3;
+  acci[0] = fmaf(q1j, tti, acci[0]);
+  acci[1] = fmaf(q2j, rinv, acci[1]);
+  acci[2] = fmaf(q2j, tti, acci[2]);
+  acci[3] = fmaf(q2j * rinv3, kki, acci[3]);
+  accj[0] = fmaf(-q1i, ttj, accj[0]);
+  accj[1] = fmaf(q2i, rinv, accj[1]);
+  accj[2] = fmaf(-q2i, ttj, accj[2]);
+  accj[3] = fmaf(-q2i * rinv3, kkj, accj[3]);
+}
+
+template <int KIND, int NTH>
+__global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const float4* __restrict__ srcA,
+                                                   const float4* __restrict__ srcB, const uint8_t* __restrict__ flags,
+                                                   int64_t ntiles, const int64_t* __restrict__ row_ptr,
+                                                   const int32_t* __restrict__ near_patch, double* __restrict__ out) {
+  constexpr int NO = 4, NW = NTH / 32, B = NTH;
+  constexpr bool kB = KIND != FAR_K1;
+  // each 32-source tile stored twice over (64 entries), so that lane t reads
+  // source (t + k) mod 32 of tile r at entry 64 r + t + k: a per-lane base
+  // address plus the step as an immediate offset
+  __shared__ float4 sA[2 * B], sB[kB ? 2 * B : 1];
+  __shared__ unsigned long long sMask[B];
+  __shared__ int sLp[B];
+  __shared__ float sRed[NW][B][NO];
+  int64_t I, J;
+  tri_pair(blockIdx.x, I, J);
+  const bool diag = I == J;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t i = I * B + tid, j = J * B + tid;
+  const int64_t P0I = (I * B) / np, P0J = (J * B) / np;
+  const bool any = flags[I * ntiles + J] != 0 || flags[J * ntiles + I] != 0;
+  {
+    const int e = 64 * warp + lane;
+    const float4 va = srcA[j];
+    sA[e] = va;
+    sA[e + 32] = va;
+    if (kB) {
+      const float4 vb = srcB[j];
+      sB[e] = vb;
+      sB[e + 32] = vb;
+    }
+  }
+  sLp[tid] = (int)(j / np - P0J);
+  unsigned long long mj = 0ull;
+  if (any && !diag && j < N)
+    for (int64_t bb = row_ptr[j]; bb < row_ptr[j + 1]; ++bb) {
+      const int64_t d = (int64_t)near_patch[bb] - P0I;
+      if (d >= 0 && d < 64) mj |= 1ull << d;
+    }
+  sMask[tid] = mj;
+  const float4 ta = srcA[i];
+  const float4 tb = kB ? srcB[i] : ta;
+  unsigned long long mi = 0ull;
+  if (any && i < N)
+    for (int64_t bb = row_ptr[i]; bb < row_ptr[i + 1]; ++bb) {
+      const int64_t d = (int64_t)near_patch[bb] - P0J;
+      if (d >= 0 && d < 64) mi |= 1ull << d;
+    }
+  const int lpi = (int)(i / np - P0I);
+  const bool pad_i = i >= N;
+  float acci[NO] = {0.f, 0.f, 0.f, 0.f};
+  __syncthreads();
+  const int up = (lane + 1) & 31;
+  if (diag) {  // the target side only (padded targets lie in this block only)
+    float none[NO] = {0.f, 0.f, 0.f, 0.f};
+    for (int s = 0; s < B; ++s) {
+      const int e = 64 * (s >> 5) + (s & 31);
+      const bool msk_i = pad_i || ((mi >> sLp[s]) & 1ull);
+      f32_pair_sym<KIND, true>(ta, tb, sA[e], kB ? sB[e] : sA[e], msk_i, true, acci, none);
+    }
+  } else {
+    // 32 x 32 warp tiles: lane t takes source (t + k) mod 32 at step k; the
+    // source sums move one lane down after each step
+    for (int r = 0; r < B / 32; ++r) {
+      float accj[NO] = {0.f, 0.f, 0.f, 0.f};
+      const float4* pa = sA + 64 * r + lane;
+      const float4* pb = kB ? sB + 64 * r + lane : pa;
+      if (!any) {
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          f32_pair_sym<KIND, false>(ta, tb, pa[k], pb[k], false, false, acci, accj);
+#pragma unroll
+          for (int o = 0; o < NO; ++o) accj[o] = __shfl_sync(0xffffffffu, accj[o], up);
+        }
+      } else {
+        for (int k = 0; k < 32; ++k) {
+          const int s = 32 * r + ((lane + k) & 31);
+          const bool msk_i = (mi >> sLp[s]) & 1ull;
+          const bool msk_j = (sMask[s] >> lpi) & 1ull;
+          f32_pair_sym<KIND, true>(ta, tb, pa[k], pb[k], msk_i, msk_j, acci, accj);
+#pragma unroll
+          for (int o = 0; o < NO; ++o) accj[o] = __shfl_sync(0xffffffffu, accj[o], up);
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < NO; ++o) sRed[warp][32 * r + lane][o] = accj[o];
+    }
+  }
+  if (!pad_i)
+#pragma unroll
+    for (int o = 0; o < NO; ++o) red_add_f64(out + o * N + i, (double)acci[o]);
+  if (diag) return;
+  __syncthreads();
+  if (j < N)
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      double v = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) v += (double)sRed[w][tid][o];
+      red_add_f64(out + o * N + j, v);
+    }
+}
+
 // flag (target block, source tile) pairs that contain a near pair
 __global__ void k_mask_flags(int64_t N, int np, int tb, int ts, int64_t ntiles, const int64_t* __restrict__ row_ptr,
                              const int32_t* __restrict__ near_patch, uint8_t* __restrict__ flags) {
@@ -505,8 +667,34 @@ static int launch_far32x2(lb_ctx* c, const void* srcA, const void* srcB, double*
 // (2); the longer kinds: the packed kernel with 4 targets per thread at its
 // natural register count (0), capped for three resident blocks per SM (1),
 // with 2 targets per thread (2).
+// the symmetric kernels (one float64 sum per accumulator: *ns = -1)
+template <int KIND>
+static int launch_far32_sym(lb_ctx* c, const void* A, const void* B, double* part, int* ns) {
+  constexpr int NTH = 128;
+  if (c->np * 62 < NTH) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
+  if (c->Npad % NTH) return lb_fail(c, LB_EINVAL, "node padding is not a multiple of the block");
+  MaskTable* m = nullptr;
+  LB_CHECK(lb_get_mask(c, NTH, NTH, &m));
+  const int64_t nb = m->ntb;
+  const int64_t nblk = nb * (nb + 1) / 2;
+  if (nblk > 0x7fffffffLL) return lb_fail(c, LB_EINVAL, "too many node blocks for one launch");
+  LB_CUDA(c, cudaMemsetAsync(part, 0, 4 * c->N * sizeof(double), c->stream));
+  ProfScope prof(c, LB_PROF_FAR32_K1 + KIND, c->N * c->N);
+  k_far32_sym<KIND, NTH><<<(unsigned)nblk, NTH, 0, c->stream>>>(c->N, c->np, (const float4*)A, (const float4*)B,
+                                                               m->flags, m->ntiles, c->row_ptr, c->near_patch, part);
+  LB_LAUNCH(c);
+  lb_pair_counter += c->N * c->N;
+  *ns = -1;
+  return LB_OK;
+}
+
+// launch variants of the single-density float32 passes (chosen by timing):
+// 0-2 the tiled kernels below, 3 the symmetric kernel (K1 and K2 only)
 #define LB_FP32_VARIANTS 3
+static int fp32_nvariants(int kind) { return (kind == FAR_K1 || kind == FAR_K2) ? 4 : LB_FP32_VARIANTS; }
 static int launch_fp32(lb_ctx* c, int kind, int variant, const void* A, const void* B, double* part, int* ns) {
+  if (variant == 3 && kind == FAR_K1) return launch_far32_sym<FAR_K1>(c, A, B, part, ns);
+  if (variant == 3 && kind == FAR_K2) return launch_far32_sym<FAR_K2>(c, A, B, part, ns);
   switch (kind) {
     case FAR_K1:
       if (variant == 1) return launch_far32x2<FAR_K1, 4, 128, 128, 3>(c, A, B, part, ns);
@@ -543,15 +731,14 @@ std::map<SingleKey, int> g_single;
 // The variant for this pass: tuned earlier in the process, or timed now on
 // the caller's data (each variant launched twice, the second timed; nothing
 // is counted or profiled), or variant 0 inside a stream capture.
-static int fp32_variant(lb_ctx* c, int kind, const void* A, const void* B, double* part, int* variant) {
-  if (c->far_order) { *variant = 0; return LB_OK; }  // oversampled sources: the scalar kernels
-  const SingleKey key{c->device, c->N, c->np, kind};
+int lb_tune_choice(lb_ctx* c, int key_kind, int nvar, int (*launch)(lb_ctx*, int, void*), void* arg, int* choice) {
+  const SingleKey key{c->device, c->N, c->np, key_kind};
   {
     std::lock_guard<std::mutex> lk(g_single_mu);
     auto it = g_single.find(key);
-    if (it != g_single.end()) { *variant = it->second; return LB_OK; }
+    if (it != g_single.end()) { *choice = it->second; return LB_OK; }
   }
-  *variant = 0;
+  *choice = 0;
   if (c->capturing) return LB_OK;
   const int prof = c->prof_on;
   const int64_t pairs = lb_pair_counter, launches = c->launches;
@@ -562,11 +749,10 @@ static int fp32_variant(lb_ctx* c, int kind, const void* A, const void* B, doubl
     rc = lb_fail(c, LB_ECUDA, "cudaEventCreate failed");
   float best_ms = 1e30f;
   int best = 0;
-  for (int v = 0; v < LB_FP32_VARIANTS && rc == LB_OK; ++v) {
-    int ns = 0;
-    rc = launch_fp32(c, kind, v, A, B, part, &ns);  // warm-up (module load, occupancy query)
+  for (int v = 0; v < nvar && rc == LB_OK; ++v) {
+    rc = launch(c, v, arg);  // warm-up (module load, occupancy query)
     if (rc == LB_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) rc = lb_fail(c, LB_ECUDA, "event record");
-    if (rc == LB_OK) rc = launch_fp32(c, kind, v, A, B, part, &ns);
+    if (rc == LB_OK) rc = launch(c, v, arg);
     if (rc == LB_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) rc = lb_fail(c, LB_ECUDA, "event record");
     float ms = 0.f;
     if (rc == LB_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
@@ -583,14 +769,43 @@ static int fp32_variant(lb_ctx* c, int kind, const void* A, const void* B, doubl
     std::lock_guard<std::mutex> lk(g_single_mu);
     g_single[key] = best;
   }
-  *variant = best;
+  *choice = best;
   return LB_OK;
 }
 
-int lb_far_tuned_variant(lb_ctx* c, int kind) {
+int lb_tuned_choice(lb_ctx* c, int key_kind) {
   std::lock_guard<std::mutex> lk(g_single_mu);
-  auto it = g_single.find(SingleKey{c->device, c->N, c->np, kind});
+  auto it = g_single.find(SingleKey{c->device, c->N, c->np, key_kind});
   return it == g_single.end() ? -1 : it->second;
+}
+
+struct Fp32Launch {
+  int kind;
+  const void *A, *B;
+  double* part;
+};
+static int fp32_launch_cb(lb_ctx* c, int v, void* arg) {
+  const Fp32Launch* a = (const Fp32Launch*)arg;
+  int ns = 0;
+  return launch_fp32(c, a->kind, v, a->A, a->B, a->part, &ns);
+}
+
+static int fp32_variant(lb_ctx* c, int kind, const void* A, const void* B, double* part, int* variant) {
+  if (c->far_order) { *variant = 0; return LB_OK; }  // oversampled sources: the scalar float32 kernels
+  Fp32Launch a{kind, A, B, part};
+  return lb_tune_choice(c, kind, fp32_nvariants(kind), fp32_launch_cb, &a, variant);
+}
+
+int lb_far_tuned_variant(lb_ctx* c, int kind) { return lb_tuned_choice(c, kind); }
+
+extern "C" int lb_debug_set_variant(lb_ctx* c, int kind, int variant) {
+  if (!c) return lb_fail(nullptr, LB_EINVAL, "null context");
+  if (!c->have_geom) return lb_fail(c, LB_ESTATE, "no geometry uploaded");
+  if (kind < 0 || kind > 3 || variant < 0 || variant >= fp32_nvariants(kind))
+    return lb_fail(c, LB_EINVAL, "no float32 launch variant %d for pass kind %d", variant, kind);
+  std::lock_guard<std::mutex> lk(g_single_mu);
+  g_single[SingleKey{c->device, c->N, c->np, kind}] = variant;
+  return LB_OK;
 }
 
 int lb_far_launch(lb_ctx* c, int kind, int prec, const void* srcA, const void* srcB, double* part, int* nsplit) {

@@ -253,16 +253,18 @@ static int launch_df_t(lb_ctx* c, const void* S, double* part, int* nsplit_out) 
 // (n_j - n_i).d' = (n_i - n_j).d).  Each CTA takes one pair of node blocks
 // (I, J), I <= J, B nodes each: thread t holds target i = I B + t and loops
 // over the sources j of block J, accumulating its own (i-side) sums in
-// registers and the j-side sums of GS sources at a time, which a warp
-// reduce-scatter (31 shuffles per 32 lanes) and a sum over the CTA's warps
-// turn into one value per source.  Diagonal blocks (I = J) take the i-side
-// only, so every ordered pair is evaluated exactly once.  The near mask
+// registers.  The j-side sums circulate: in each 32 x 32 warp tile lane t
+// takes source (t + k) mod 32 at step k and hands its j-side sums one lane
+// down after it (eight shuffles per step), so that after 32 steps lane t
+// holds the warp's sums for source t; a sum over the CTA's warps in shared
+// memory follows.  Diagonal blocks (I = J) take the i-side only, so every
+// ordered pair is evaluated exactly once.  The near mask
 // holds per direction (Near is not symmetric): bit patch(j) of Near(i) for
 // the i-side, bit patch(i) of Near(j), gathered per source into shared
 // memory, for the j-side.  Sums leave each CTA as float64 additions to
 // out[4][N] (red.global.add.f64): the order of those additions, and so the
 // last bit of the result, is not fixed from run to run.
-template <int KIND>
+template <int KIND, bool MASKED = true>
 __device__ __forceinline__ void df_pair_sym(const float* t, const float4& A, const float4& B, const float4& C,
                                             const float4& D, bool mi, bool mj, F2* acci, F2* accj) {
   // t: x_hi[3], x_lo[3], n_hi[3], n_lo[3], q1 (hi, lo), q2 (hi, lo) of the target
@@ -271,10 +273,10 @@ __device__ __forceinline__ void df_pair_sym(const float* t, const float4& A, con
   const F2 dz = fast_two_sum(t[2] - A.z, t[5] - B.z);
   const F2 r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
   F2 rinv = df_rsqrt(r2);
-  if (mi && mj) rinv = {0.f, 0.f};  // both directions masked (the self pair, padding)
+  if (MASKED && mi && mj) rinv = {0.f, 0.f};  // both directions masked (the self pair, padding)
   const F2 zero = {0.f, 0.f};
-  const F2 q1j = mi ? zero : F2{A.w, B.w};    // source charges, i-side
-  const F2 q1i = mj ? zero : F2{t[12], t[13]};  // target charges, j-side
+  const F2 q1j = MASKED && mi ? zero : F2{A.w, B.w};    // source charges, i-side
+  const F2 q1i = MASKED && mj ? zero : F2{t[12], t[13]};  // target charges, j-side
   const F2 rinv2 = df_sqr(rinv);
   const F2 rinv3 = df_mul(rinv2, rinv);
   if (KIND == FAR_K1) {
@@ -292,8 +294,8 @@ __device__ __forceinline__ void df_pair_sym(const float* t, const float4& A, con
     return;
   }
   // FAR_K2: q1 = mu1, q2 = mu2
-  const F2 q2j = mi ? zero : F2{C.w, D.w};
-  const F2 q2i = mj ? zero : F2{t[14], t[15]};
+  const F2 q2j = MASKED && mi ? zero : F2{C.w, D.w};
+  const F2 q2i = MASKED && mj ? zero : F2{t[14], t[15]};
   const F2 nxx = {t[6], t[9]}, nxy = {t[7], t[10]}, nxz = {t[8], t[11]};
   const F2 nyx = {C.x, D.x}, nyy = {C.y, D.y}, nyz = {C.z, D.z};
   const F2 a = df_dot3(nxx, nxy, nxz, dx, dy, dz);  // n_i.d
@@ -316,33 +318,24 @@ __device__ __forceinline__ void df_pair_sym(const float* t, const float4& A, con
   df_acc(accj[3], df_mul(df_mul(F2{-q2i.h, -q2i.l}, rinv3), kkj));
 }
 
-__device__ __forceinline__ void red_add_f64(double* p, double v) {
-  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
-}
-
-template <int KIND, int B, int GS>
-__global__ void __launch_bounds__(B) k_far_df_sym(int64_t N, int np, int nb, const float4* __restrict__ S,
-                                                  int64_t Npad, const uint8_t* __restrict__ flags, int64_t ntiles,
-                                                  const int64_t* __restrict__ row_ptr,
-                                                  const int32_t* __restrict__ near_patch, double* __restrict__ out) {
-  constexpr int NO = 4, NW = B / 32;
-  static_assert(GS * NO <= 32 && (GS * NO & (GS * NO - 1)) == 0, "reduce-scatter width");
+template <int KIND, int NTH>
+__global__ void __launch_bounds__(NTH) k_far_df_sym(int64_t N, int np, int nb, const float4* __restrict__ S,
+                                                    int64_t Npad, const uint8_t* __restrict__ flags, int64_t ntiles,
+                                                    const int64_t* __restrict__ row_ptr,
+                                                    const int32_t* __restrict__ near_patch, double* __restrict__ out) {
+  constexpr int NO = 4, NW = NTH / 32, B = NTH;
   __shared__ float4 sA[B], sB[B], sC[B], sD[B];
   __shared__ unsigned long long sMask[B];
   __shared__ int sLp[B];
   __shared__ F2 sRed[NW][B][NO];
-  // block pair (I, J), I <= J, from the linear index J (J + 1) / 2 + I
-  const int64_t lin = blockIdx.x;
-  int64_t J = (int64_t)((sqrt(8.0 * (double)lin + 1.0) - 1.0) * 0.5);
-  while (J * (J + 1) / 2 > lin) --J;
-  while ((J + 1) * (J + 2) / 2 <= lin) ++J;
-  const int64_t I = lin - J * (J + 1) / 2;
+  int64_t I, J;
+  tri_pair(blockIdx.x, I, J);
   const bool diag = I == J;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t i = I * B + tid, j = J * B + tid;
   const int64_t P0I = (I * B) / np, P0J = (J * B) / np;
   const bool any = flags[I * ntiles + J] != 0 || flags[J * ntiles + I] != 0;
-  // stage block J and the j-side masks; load the target
+  // stage block J with its j-side masks (bit p: patch P0I + p in Near(j))
   sA[tid] = S[j];
   sB[tid] = S[Npad + j];
   sC[tid] = S[2 * Npad + j];
@@ -355,14 +348,7 @@ __global__ void __launch_bounds__(B) k_far_df_sym(int64_t N, int np, int nb, con
       if (d >= 0 && d < 64) mj |= 1ull << d;
     }
   sMask[tid] = mj;
-  unsigned long long mi = 0ull;
-  if (any && i < N)
-    for (int64_t bb = row_ptr[i]; bb < row_ptr[i + 1]; ++bb) {
-      const int64_t d = (int64_t)near_patch[bb] - P0J;
-      if (d >= 0 && d < 64) mi |= 1ull << d;
-    }
-  const int lpi = (int)(i / np - P0I);
-  const bool pad_i = i >= N;
+  // the target: data, i-side mask over block J's patches, patch offset
   float tv[16];
   {
     const float4 a = S[i], b = S[Npad + i], c = S[2 * Npad + i], d = S[3 * Npad + i];
@@ -372,29 +358,53 @@ __global__ void __launch_bounds__(B) k_far_df_sym(int64_t N, int np, int nb, con
     tv[9] = d.x; tv[10] = d.y; tv[11] = d.z;
     tv[12] = a.w; tv[13] = b.w; tv[14] = c.w; tv[15] = d.w;
   }
+  unsigned long long mi = 0ull;
+  if (any && i < N)
+    for (int64_t bb = row_ptr[i]; bb < row_ptr[i + 1]; ++bb) {
+      const int64_t d = (int64_t)near_patch[bb] - P0J;
+      if (d >= 0 && d < 64) mi |= 1ull << d;
+    }
+  const int lpi = (int)(i / np - P0I);
+  const bool pad_i = i >= N;
   F2 acci[NO];
 #pragma unroll
   for (int o = 0; o < NO; ++o) acci[o] = {0.f, 0.f};
   __syncthreads();
-  for (int g = 0; g < B; g += GS) {
-    F2 accj[GS * NO];
-#pragma unroll
-    for (int k = 0; k < GS * NO; ++k) accj[k] = {0.f, 0.f};
-#pragma unroll
-    for (int u = 0; u < GS; ++u) {
-      const int s = g + u;
+  if (diag) {  // the target side only, every source of the block in turn
+    F2 none[NO] = {};  // j-side sums of the diagonal: charges masked, never read
+    for (int s = 0; s < B; ++s) {
       const bool msk_i = pad_i || ((mi >> sLp[s]) & 1ull);
-      const bool msk_j = diag || pad_i || ((sMask[s] >> lpi) & 1ull);
-      df_pair_sym<KIND>(tv, sA[s], sB[s], sC[s], sD[s], msk_i, msk_j, acci, accj + u * NO);
+      df_pair_sym<KIND>(tv, sA[s], sB[s], sC[s], sD[s], msk_i, true, acci, none);
     }
-    if (!diag) {
-      warp_reduce_scatter<GS * NO>(accj, lane);
-      // value k = u NO + o ends in lanes k << (5 - log2(GS NO)) and up
-      constexpr int SH = 5 - Log2<GS * NO>::value;
-      if ((lane & ((1 << SH) - 1)) == 0) {
-        const int k = lane >> SH;
-        sRed[warp][g + k / NO][k % NO] = accj[0];
+  } else {
+    // 32 x 32 warp tiles: at step k lane t takes source (t + k) mod 32 of the
+    // tile, and the source-side sums move one lane down after each step, so
+    // that lane t holds the sums of source (t + k) mod 32 throughout and of
+    // source t after the 32nd step
+    for (int r = 0; r < B / 32; ++r) {
+      F2 accj[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) accj[o] = {0.f, 0.f};
+      if (!any) {  // no near pair in either direction (and no padded target off the diagonal)
+#pragma unroll 2
+        for (int k = 0; k < 32; ++k) {
+          const int s = 32 * r + ((lane + k) & 31);
+          df_pair_sym<KIND, false>(tv, sA[s], sB[s], sC[s], sD[s], false, false, acci, accj);
+#pragma unroll
+          for (int o = 0; o < NO; ++o) accj[o] = shfl_idx_v(accj[o], (lane + 1) & 31);
+        }
+      } else {
+        for (int k = 0; k < 32; ++k) {
+          const int s = 32 * r + ((lane + k) & 31);
+          const bool msk_i = (mi >> sLp[s]) & 1ull;
+          const bool msk_j = (sMask[s] >> lpi) & 1ull;
+          df_pair_sym<KIND>(tv, sA[s], sB[s], sC[s], sD[s], msk_i, msk_j, acci, accj);
+#pragma unroll
+          for (int o = 0; o < NO; ++o) accj[o] = shfl_idx_v(accj[o], (lane + 1) & 31);
+        }
       }
+#pragma unroll
+      for (int o = 0; o < NO; ++o) sRed[warp][32 * r + lane][o] = accj[o];
     }
   }
   if (!pad_i)
@@ -414,7 +424,7 @@ __global__ void __launch_bounds__(B) k_far_df_sym(int64_t N, int np, int nb, con
 
 template <int KIND>
 static int launch_df_sym(lb_ctx* c, const void* S, double* part) {
-  constexpr int B = 128, GS = 4;
+  constexpr int NTH = 128, B = NTH;
   if (c->np * 62 < B) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
   if (c->Npad % B) return lb_fail(c, LB_EINVAL, "node padding is not a multiple of the block");
   MaskTable* m = nullptr;
@@ -425,9 +435,8 @@ static int launch_df_sym(lb_ctx* c, const void* S, double* part) {
   LB_CUDA(c, cudaMemsetAsync(part, 0, 4 * c->N * sizeof(double), c->stream));
   const int64_t pairs = c->N * c->N;
   ProfScope prof(c, LB_PROF_FARDF_K1 + KIND, pairs);
-  k_far_df_sym<KIND, B, GS><<<(unsigned)nblk, B, 0, c->stream>>>(c->N, c->np, (int)nb, (const float4*)S, c->Npad,
-                                                                  m->flags, m->ntiles, c->row_ptr, c->near_patch,
-                                                                  part);
+  k_far_df_sym<KIND, NTH><<<(unsigned)nblk, NTH, 0, c->stream>>>(c->N, c->np, (int)nb, (const float4*)S, c->Npad,
+                                                                m->flags, m->ntiles, c->row_ptr, c->near_patch, part);
   LB_LAUNCH(c);
   lb_pair_counter += pairs;
   return LB_OK;

@@ -262,6 +262,14 @@ int lb_pack_df_points(lb_ctx* c, int64_t n, int64_t npad, const double* Y, const
 int lb_far_launch_df(lb_ctx* c, int kind, const void* S, double* part, int* nsplit);
 // launch variant chosen for single-density float32 passes of `kind`, -1 if not tuned yet
 int lb_far_tuned_variant(lb_ctx* c, int kind);
+// Timing-based choice among nvar launch variants of one pass (launch(c, v,
+// arg) runs variant v): each is launched twice, the second timed, once per
+// (device, N, n_p, key_kind) and process; the fastest is kept.  Variant 0
+// while a graph is being captured and nothing is tuned yet.  key_kind 0..3:
+// the float32 single-density kinds.
+int lb_tune_choice(lb_ctx* c, int key_kind, int nvar, int (*launch)(lb_ctx*, int, void*), void* arg, int* choice);
+// the choice made for key_kind, -1 if not tuned yet
+int lb_tuned_choice(lb_ctx* c, int key_kind);
 // A3 applied to R densities tau[R][N] -> out[R][N] with several densities per
 // far-field pass (prec LB_FP32 or LB_DF64); u (may be null) receives S[S[tau]]
 int lb_apply_a3_batch(lb_ctx* c, int prec, int R, const double* tau, double* out, double* u);
