@@ -66,9 +66,14 @@ FLOPS_PER_PAIR = {"k1": 20, "kall": 45, "k2": 43, "k4": 21}
 # of a pass, and flops per pair and density
 FLOPS_BATCH = {"k1": (10, 9), "k2": (35, 8)}
 # double-float kernels (csrc/far_df.cu): float32 operations per pair, FMA = 2
-# (TwoSum 6, pair add 8, pair product 7, square 6, rsqrt with Newton step 17,
-# accumulate 8)
-DF_FLOPS_PER_PAIR = {"k1": 137, "kall": 320, "k2": 326, "k4": 150}
+# (TwoSum 6, FastTwoSum 3, pair add 8, pair product 7, square 6, rsqrt with
+# Newton step 17, accumulate 8; d renormalised, 15)
+DF_FLOPS_PER_PAIR = {"k1": 146, "kall": 329, "k2": 335, "k4": 159}
+# symmetric kernels (A3 passes; far.cu k_far32_sym, far_df.cu k_far_df_sym):
+# flops of one unordered pair, both directions, halved to a per-ordered-pair
+# figure: float32 K1 28 / 2, K2 56 / 2; double-float K1 213 / 2, K2 396 / 2
+SYM_FLOPS_PER_PAIR = {"k1": 14.0, "k2": 28.0}
+DF_SYM_FLOPS_PER_PAIR = {"k1": 106.5, "k2": 198.0}
 
 
 def _dist():
@@ -307,6 +312,7 @@ def run_ours(args):
     sm_count = ctx.info()["sm_count"]
     clk_mhz = clocks.get("sm_mhz") or (peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1440.0)
     cats = {k: v for k, v in prof.items() if isinstance(v, dict) and k.startswith("far")}
+    tuning = ctx.get_tuning()
     dom = max(cats, key=lambda k: cats[k]["ms"]) if cats else None
     roofline = None
     nrhs = fb.shape[0]
@@ -322,12 +328,15 @@ def run_ours(args):
             flops = s.N * s.N * (sh + pd * per_launch_dens)
             peak, note, kname = fp32_peak, fp32_note, f"k_farb32<{dom}>"
         elif dom.startswith("far32"):
-            flops = s.N * s.N * FLOPS_PER_PAIR[kind]
-            peak, note, kname = fp32_peak, fp32_note, f"k_far<{dom}>"
+            sym = (tuning.get(f"far32_single_{kind}") or "").startswith("symmetric")
+            flops = s.N * s.N * (SYM_FLOPS_PER_PAIR[kind] if sym else FLOPS_PER_PAIR[kind])
+            peak, note = fp32_peak, fp32_note
+            kname = f"k_far32_sym<{dom}>" if sym else f"k_far<{dom}>"
         elif dom.startswith("fardf"):
-            flops = s.N * s.N * DF_FLOPS_PER_PAIR[kind]
-            peak, note, kname = fp32_peak, fp32_note + " (double-float arithmetic in float32 operations)", \
-                f"k_far_df<{dom}>"
+            sym = kind in DF_SYM_FLOPS_PER_PAIR
+            flops = s.N * s.N * (DF_SYM_FLOPS_PER_PAIR[kind] if sym else DF_FLOPS_PER_PAIR[kind])
+            peak, note = fp32_peak, fp32_note + " (double-float arithmetic in float32 operations)"
+            kname = f"k_far_df_sym<{dom}>" if sym else f"k_far_df<{dom}>"
         else:
             flops = s.N * s.N * FLOPS_PER_PAIR[kind]
             peak = 1.25 * clk_mhz / 2070.0
@@ -522,6 +531,7 @@ def torus_batch_record(lb, torch, device, stream, flush, steps=3, warmup=3):
     ctx.set_profiling(False)
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
     cats = {k: v for k, v in prof.items() if isinstance(v, dict) and k.startswith("far")}
+    tuning = ctx.get_tuning()
     dom = max(cats, key=lambda k: cats[k]["ms"])
     # one plain float64 solve of the first right-hand side, timed
     ctx.set_params(lb.default_params(eps_quad=1e-12, tol=1e-10, precision=lb.LB_FP64, formulation=lb.LB_A3))

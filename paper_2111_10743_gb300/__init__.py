@@ -228,8 +228,9 @@ class Context:
             for k, kn in enumerate(("k1", "k2")):
                 for r, rn in enumerate(("rc4", "rc8")):
                     out[f"{pn}_{kn}_{rn}"] = names[a[p * 4 + k * 2 + r]]
-        pk = ("packed_nt4", "packed_nt4_3blocks", "packed_nt2", "symmetric")
-        single = {0: ("scalar_nt4", "packed_nt4", "scalar_nt8", "symmetric"), 1: pk, 2: pk, 3: pk}
+        sym = ("symmetric", "symmetric_packed")
+        pk = ("packed_nt4", "packed_nt4_3blocks", "packed_nt2") + sym
+        single = {0: ("scalar_nt4", "packed_nt4", "scalar_nt8") + sym, 1: pk, 2: pk, 3: pk}
         for kind, kn in enumerate(("k1", "kall", "k2", "k4")):
             v = a[8 + kind]
             out[f"far32_single_{kn}"] = single[kind][v] if v >= 0 else None

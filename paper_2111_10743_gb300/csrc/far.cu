@@ -429,7 +429,7 @@ __device__ __forceinline__ void f32_pair_sym(const float4& ta, const float4& tb,
     if (mi) q1j = 0.f;
     if (mj) q1i = 0.f;
   }
-  const float rinv3 = rinv * rinv * rinv;
+  const float rinv2 = rinv * rinv, rinv3 = rinv2 * rinv;
   if (KIND == FAR_K1) {
     acci[0] = fmaf(q1j, rinv, acci[0]);
     accj[0] = fmaf(q1i, rinv, accj[0]);
@@ -452,7 +452,7 @@ __device__ __forceinline__ void f32_pair_sym(const float4& ta, const float4& tb,
   const float cn = fmaf(ez, dz, fmaf(ey, dy, ex * dx));          // (n_i - n_j).d
   const float bn = an - cn;                                      // n_j.d
   const float hd = 0.5f * fmaf(ez, ez, fmaf(ey, ey, ex * ex));  // 1 - n_i.n_j
-  const float c3 = cn * (3.f * rinv * rinv);
+  const float c3 = cn * (3.f * rinv2);
   // target i: 3 a c / r^2 - hd; target j: -(3 b c / r^2 + hd)
   const float kki = fmaf(an, c3, -hd), kkj = fmaf(bn, c3, hd);
   const float tti = an * rinv3, ttj = bn * rinv3;
@@ -466,7 +466,56 @@ __device__ __forceinline__ void f32_pair_sym(const float4& ta, const float4& tb,
   accj[3] = fmaf(-q2i * rinv3, kkj, accj[3]);
 }
 
-template <int KIND, int NTH>
+// Two unordered pairs at once in packed f32x2 arithmetic: one target
+// (components splatted in both halves) against two consecutive sources (one
+// per half).  T: target x, y, z, n_x, n_y, n_z; QI1, QI2 its charges and
+// QI1N = -QI1; S: packed source x, y, z, q1, n_x, n_y, n_z, q2.  acci: the
+// target's sums per source half; accj: the two sources' sums.
+template <int KIND>
+__device__ __forceinline__ void pair2_sym(const u64* T, u64 QI1, u64 QI1N, u64 QI2, const u64* S, u64* acci,
+                                          u64* accj, const u64 three, const u64 mhalf) {
+  const u64 dx = sub2(T[0], S[0]), dy = sub2(T[1], S[1]), dz = sub2(T[2], S[2]);
+  const u64 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+  const u64 rinv = rsqrt2(r2);
+  const u64 rinv2 = mul2(rinv, rinv), rinv3 = mul2(rinv2, rinv);
+  if (KIND == FAR_K1) {
+    acci[0] = fma2(S[3], rinv, acci[0]);
+    accj[0] = fma2(QI1, rinv, accj[0]);
+    const u64 tj = mul2(S[3], rinv3), tin = mul2(QI1N, rinv3);
+    acci[1] = fma2(tj, dx, acci[1]);
+    acci[2] = fma2(tj, dy, acci[2]);
+    acci[3] = fma2(tj, dz, acci[3]);
+    accj[1] = fma2(tin, dx, accj[1]);
+    accj[2] = fma2(tin, dy, accj[2]);
+    accj[3] = fma2(tin, dz, accj[3]);
+    return;
+  }
+  const u64 an = fma2(T[5], dz, fma2(T[4], dy, mul2(T[3], dx)));       // n_i.d
+  const u64 ex = sub2(T[3], S[4]), ey = sub2(T[4], S[5]), ez = sub2(T[5], S[6]);
+  const u64 cn = fma2(ez, dz, fma2(ey, dy, mul2(ex, dx)));             // (n_i - n_j).d
+  const u64 bneg = sub2(cn, an);                                       // -n_j.d
+  const u64 hdn = mul2(mhalf, fma2(ez, ez, fma2(ey, ey, mul2(ex, ex))));  // -(1 - n_i.n_j)
+  const u64 c3 = mul2(cn, mul2(three, rinv2));
+  const u64 kki = fma2(an, c3, hdn);     // 3 a c / r^2 - (1 - n_i.n_j)
+  const u64 kkjn = fma2(bneg, c3, hdn);  // -(3 b c / r^2 + 1 - n_i.n_j)
+  const u64 tti = mul2(an, rinv3), ttjn = mul2(bneg, rinv3);
+  acci[0] = fma2(S[3], tti, acci[0]);
+  acci[1] = fma2(S[7], rinv, acci[1]);
+  acci[2] = fma2(S[7], tti, acci[2]);
+  acci[3] = fma2(mul2(S[7], rinv3), kki, acci[3]);
+  accj[0] = fma2(QI1, ttjn, accj[0]);
+  accj[1] = fma2(QI2, rinv, accj[1]);
+  accj[2] = fma2(QI2, ttjn, accj[2]);
+  accj[3] = fma2(mul2(QI2, rinv3), kkjn, accj[3]);
+}
+
+__device__ __forceinline__ u64 shfl_u64(u64 v, int src) {
+  float a, b;
+  upk2(v, a, b);
+  return pk2(__shfl_sync(0xffffffffu, a, src), __shfl_sync(0xffffffffu, b, src));
+}
+
+template <int KIND, int NTH, bool PACKED>
 __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const float4* __restrict__ srcA,
                                                    const float4* __restrict__ srcB, const uint8_t* __restrict__ flags,
                                                    int64_t ntiles, const int64_t* __restrict__ row_ptr,
@@ -477,6 +526,12 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
   // source (t + k) mod 32 of tile r at entry 64 r + t + k: a per-lane base
   // address plus the step as an immediate offset
   __shared__ float4 sA[2 * B], sB[kB ? 2 * B : 1];
+  // packed loop: the same tiles pair-interleaved, entry e of tile r holding
+  // (c_e, c_(e+1)) for two components c per plane, sources e and e + 1 mod
+  // 32 (planes: x y, z q1, n_x n_y, n_z q2), so that one 16-byte load gives
+  // two packed operands
+  constexpr int NPL = PACKED ? (kB ? 4 : 2) : 1;
+  __shared__ float4 sP[NPL][PACKED ? 2 * B : 1];
   __shared__ unsigned long long sMask[B];
   __shared__ int sLp[B];
   __shared__ float sRed[NW][B][NO];
@@ -490,12 +545,30 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
   {
     const int e = 64 * warp + lane;
     const float4 va = srcA[j];
+    const float4 vb = kB ? srcB[j] : va;
     sA[e] = va;
     sA[e + 32] = va;
     if (kB) {
-      const float4 vb = srcB[j];
       sB[e] = vb;
       sB[e + 32] = vb;
+    }
+    if (PACKED) {
+      // this source is the first element of entries lane, lane + 32 and the
+      // second of entries lane - 1 (mod 64) and lane + 31
+      const float c[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+      const int f0 = 64 * warp + lane, f1 = f0 + 32;
+      const int g0 = 64 * warp + ((lane + 63) & 63), g1 = 64 * warp + lane + 31;
+#pragma unroll
+      for (int p = 0; p < NPL; ++p) {
+        float* a0 = reinterpret_cast<float*>(&sP[p][f0]);
+        float* a1 = reinterpret_cast<float*>(&sP[p][f1]);
+        float* b0 = reinterpret_cast<float*>(&sP[p][g0]);
+        float* b1 = reinterpret_cast<float*>(&sP[p][g1]);
+        a0[0] = a1[0] = c[2 * p];
+        a0[2] = a1[2] = c[2 * p + 1];
+        b0[1] = b1[1] = c[2 * p];
+        b0[3] = b1[3] = c[2 * p + 1];
+      }
     }
   }
   sLp[tid] = (int)(j / np - P0J);
@@ -533,7 +606,40 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
       float accj[NO] = {0.f, 0.f, 0.f, 0.f};
       const float4* pa = sA + 64 * r + lane;
       const float4* pb = kB ? sB + 64 * r + lane : pa;
-      if (!any) {
+      if (!any && PACKED) {
+        // lane t takes sources t + 2k and t + 2k + 1 at step k; its two
+        // source-sum slots move two lanes down after each step, so that lane
+        // t ends with source t in the low slot and source t + 1 in the high
+        const u64 T[6] = {pk2(ta.x, ta.x), pk2(ta.y, ta.y), pk2(ta.z, ta.z),
+                          pk2(tb.x, tb.x), pk2(tb.y, tb.y), pk2(tb.z, tb.z)};
+        const u64 QI1 = pk2(ta.w, ta.w), QI1N = pk2(-ta.w, -ta.w), QI2 = pk2(tb.w, tb.w);
+        const u64 three = pk2(3.f, 3.f), mhalf = pk2(-0.5f, -0.5f);
+        const int up2 = (lane + 2) & 31;
+        u64 ai[NO] = {0ull, 0ull, 0ull, 0ull}, aj[NO] = {0ull, 0ull, 0ull, 0ull};
+        const float4* q = &sP[0][64 * r + lane];
+#pragma unroll 4
+        for (int k = 0; k < 16; ++k) {
+          u64 S[8];
+#pragma unroll
+          for (int p = 0; p < NPL; ++p) {
+            const float4 v = q[p * 2 * B + 2 * k];
+            S[2 * p] = pk2(v.x, v.y);
+            S[2 * p + 1] = pk2(v.z, v.w);
+          }
+          pair2_sym<KIND>(T, QI1, QI1N, QI2, S, ai, aj, three, mhalf);
+#pragma unroll
+          for (int o = 0; o < NO; ++o) aj[o] = shfl_u64(aj[o], up2);
+        }
+        const int dn = (lane + 31) & 31;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) {
+          float lo, hi;
+          upk2(ai[o], lo, hi);
+          acci[o] += lo + hi;
+          upk2(aj[o], lo, hi);
+          accj[o] = lo + __shfl_sync(0xffffffffu, hi, dn);  // source t: low slot here, high slot of lane t - 1
+        }
+      } else if (!any) {
 #pragma unroll 8
         for (int k = 0; k < 32; ++k) {
           f32_pair_sym<KIND, false>(ta, tb, pa[k], pb[k], false, false, acci, accj);
@@ -668,7 +774,7 @@ static int launch_far32x2(lb_ctx* c, const void* srcA, const void* srcB, double*
 // natural register count (0), capped for three resident blocks per SM (1),
 // with 2 targets per thread (2).
 // the symmetric kernels (one float64 sum per accumulator: *ns = -1)
-template <int KIND>
+template <int KIND, bool PACKED>
 static int launch_far32_sym(lb_ctx* c, const void* A, const void* B, double* part, int* ns) {
   constexpr int NTH = 128;
   if (c->np * 62 < NTH) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
@@ -680,7 +786,7 @@ static int launch_far32_sym(lb_ctx* c, const void* A, const void* B, double* par
   if (nblk > 0x7fffffffLL) return lb_fail(c, LB_EINVAL, "too many node blocks for one launch");
   LB_CUDA(c, cudaMemsetAsync(part, 0, 4 * c->N * sizeof(double), c->stream));
   ProfScope prof(c, LB_PROF_FAR32_K1 + KIND, c->N * c->N);
-  k_far32_sym<KIND, NTH><<<(unsigned)nblk, NTH, 0, c->stream>>>(c->N, c->np, (const float4*)A, (const float4*)B,
+  k_far32_sym<KIND, NTH, PACKED><<<(unsigned)nblk, NTH, 0, c->stream>>>(c->N, c->np, (const float4*)A, (const float4*)B,
                                                                m->flags, m->ntiles, c->row_ptr, c->near_patch, part);
   LB_LAUNCH(c);
   lb_pair_counter += c->N * c->N;
@@ -689,12 +795,15 @@ static int launch_far32_sym(lb_ctx* c, const void* A, const void* B, double* par
 }
 
 // launch variants of the single-density float32 passes (chosen by timing):
-// 0-2 the tiled kernels below, 3 the symmetric kernel (K1 and K2 only)
+// 0-2 the tiled kernels below; K1 and K2 also 3, the symmetric kernel, and
+// 4, the same with the packed two-source loop
 #define LB_FP32_VARIANTS 3
-static int fp32_nvariants(int kind) { return (kind == FAR_K1 || kind == FAR_K2) ? 4 : LB_FP32_VARIANTS; }
+static int fp32_nvariants(int kind) { return (kind == FAR_K1 || kind == FAR_K2) ? 5 : LB_FP32_VARIANTS; }
 static int launch_fp32(lb_ctx* c, int kind, int variant, const void* A, const void* B, double* part, int* ns) {
-  if (variant == 3 && kind == FAR_K1) return launch_far32_sym<FAR_K1>(c, A, B, part, ns);
-  if (variant == 3 && kind == FAR_K2) return launch_far32_sym<FAR_K2>(c, A, B, part, ns);
+  if (variant == 3 && kind == FAR_K1) return launch_far32_sym<FAR_K1, false>(c, A, B, part, ns);
+  if (variant == 3 && kind == FAR_K2) return launch_far32_sym<FAR_K2, false>(c, A, B, part, ns);
+  if (variant == 4 && kind == FAR_K1) return launch_far32_sym<FAR_K1, true>(c, A, B, part, ns);
+  if (variant == 4 && kind == FAR_K2) return launch_far32_sym<FAR_K2, true>(c, A, B, part, ns);
   switch (kind) {
     case FAR_K1:
       if (variant == 1) return launch_far32x2<FAR_K1, 4, 128, 128, 3>(c, A, B, part, ns);

@@ -358,7 +358,10 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
     for (int s = 0; s < p.max_refine && !ok; ++s) {
       int its = 0;
       double ires = 0;
-      LB_CHECK(gmres(c, LB_FP32, r, delta, p.inner_tol, p.max_iter, &its, &ires, nullptr));
+      // once the residual r_s is known (rel = |r_s| / |b|), the inner solve
+      // need only take it to half the target: tol |b| / 2
+      const double itol = s == 0 ? p.inner_tol : std::max(p.inner_tol, std::min(0.5, 0.5 * p.tol / rel));
+      LB_CHECK(gmres(c, LB_FP32, r, delta, itol, p.max_iter, &its, &ires, nullptr));
       it += its;
       k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, delta, 1.0, sigma);
       LB_LAUNCH(c);
