@@ -359,8 +359,9 @@ int lb_geometry_gradient(lb_ctx* ctx, int nrhs, const double* f, const double* g
  * with 8 targets per thread; the others: 0 packed with 4 targets per thread,
  * 1 the same with registers capped for three resident blocks per SM, 2
  * packed with 2 targets per thread; K1 and A3 pass 2 also 3: each unordered
- * node pair evaluated once for both directions, and 4: the same with two
- * sources per packed instruction), -1 = not tuned yet.
+ * node pair evaluated once for both directions, 4: the same with two
+ * sources per packed instruction, 5 and 6: 3 and 4 with two targets per
+ * thread), -1 = not tuned yet.
  * shapes: host memory of 12 ints. */
 int lb_get_tuning(lb_ctx* ctx, int* shapes);
 
@@ -410,7 +411,7 @@ int lb_debug_fail_alloc(lb_ctx* ctx, int64_t after);
  * paper): variant v (as reported in lb_get_tuning's shapes[8 + kind]) is
  * used for pass `kind` (0..3) on this context's surface from now on, in this
  * process, in place of the timed choice.  LB_EINVAL for a kind or variant out
- * of range (variants 3 and 4 exist for kinds 0 and 2 only); LB_ESTATE before a
+ * of range (variants 3 to 6 exist for kinds 0 and 2 only); LB_ESTATE before a
  * geometry is uploaded. */
 int lb_debug_set_variant(lb_ctx* ctx, int kind, int variant);
 

@@ -228,7 +228,7 @@ class Context:
             for k, kn in enumerate(("k1", "k2")):
                 for r, rn in enumerate(("rc4", "rc8")):
                     out[f"{pn}_{kn}_{rn}"] = names[a[p * 4 + k * 2 + r]]
-        sym = ("symmetric", "symmetric_packed")
+        sym = ("symmetric", "symmetric_packed", "symmetric_nt2", "symmetric_packed_nt2")
         pk = ("packed_nt4", "packed_nt4_3blocks", "packed_nt2") + sym
         single = {0: ("scalar_nt4", "packed_nt4", "scalar_nt8") + sym, 1: pk, 2: pk, 3: pk}
         for kind, kn in enumerate(("k1", "kall", "k2", "k4")):

@@ -515,12 +515,16 @@ __device__ __forceinline__ u64 shfl_u64(u64 v, int src) {
   return pk2(__shfl_sync(0xffffffffu, a, src), __shfl_sync(0xffffffffu, b, src));
 }
 
-template <int KIND, int NTH, bool PACKED>
-__global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const float4* __restrict__ srcA,
-                                                   const float4* __restrict__ srcB, const uint8_t* __restrict__ flags,
-                                                   int64_t ntiles, const int64_t* __restrict__ row_ptr,
-                                                   const int32_t* __restrict__ near_patch, double* __restrict__ out) {
-  constexpr int NO = 4, NW = NTH / 32, B = NTH;
+// NT: targets per lane (the CTA has 128 / NT threads for a 128-node block),
+// so that each source load and each rotation step serves NT pairs
+template <int KIND, bool PACKED, int NT>
+__global__ void __launch_bounds__(128 / NT) k_far32_sym(int64_t N, int np, const float4* __restrict__ srcA,
+                                                        const float4* __restrict__ srcB,
+                                                        const uint8_t* __restrict__ flags, int64_t ntiles,
+                                                        const int64_t* __restrict__ row_ptr,
+                                                        const int32_t* __restrict__ near_patch,
+                                                        double* __restrict__ out) {
+  constexpr int NO = 4, B = 128, NTH = B / NT, NW = NTH / 32;
   constexpr bool kB = KIND != FAR_K1;
   // each 32-source tile stored twice over (64 entries), so that lane t reads
   // source (t + k) mod 32 of tile r at entry 64 r + t + k: a per-lane base
@@ -539,11 +543,13 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
   tri_pair(blockIdx.x, I, J);
   const bool diag = I == J;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t i = I * B + tid, j = J * B + tid;
   const int64_t P0I = (I * B) / np, P0J = (J * B) / np;
   const bool any = flags[I * ntiles + J] != 0 || flags[J * ntiles + I] != 0;
-  {
-    const int e = 64 * warp + lane;
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {  // stage block J: this thread's sources ls = tid + u NTH
+    const int ls = tid + u * NTH, rt = ls >> 5;
+    const int64_t j = J * B + ls;
+    const int e = 64 * rt + lane;
     const float4 va = srcA[j];
     const float4 vb = kB ? srcB[j] : va;
     sA[e] = va;
@@ -554,10 +560,10 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
     }
     if (PACKED) {
       // this source is the first element of entries lane, lane + 32 and the
-      // second of entries lane - 1 (mod 64) and lane + 31
+      // second of entries lane - 1 (mod 64) and lane + 31 of its tile
       const float c[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-      const int f0 = 64 * warp + lane, f1 = f0 + 32;
-      const int g0 = 64 * warp + ((lane + 63) & 63), g1 = 64 * warp + lane + 31;
+      const int f0 = 64 * rt + lane, f1 = f0 + 32;
+      const int g0 = 64 * rt + ((lane + 63) & 63), g1 = 64 * rt + lane + 31;
 #pragma unroll
       for (int p = 0; p < NPL; ++p) {
         float* a0 = reinterpret_cast<float*>(&sP[p][f0]);
@@ -570,34 +576,48 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
         b0[3] = b1[3] = c[2 * p + 1];
       }
     }
+    sLp[ls] = (int)(j / np - P0J);
+    unsigned long long mj = 0ull;
+    if (any && !diag && j < N)
+      for (int64_t bb = row_ptr[j]; bb < row_ptr[j + 1]; ++bb) {
+        const int64_t d = (int64_t)near_patch[bb] - P0I;
+        if (d >= 0 && d < 64) mj |= 1ull << d;
+      }
+    sMask[ls] = mj;
   }
-  sLp[tid] = (int)(j / np - P0J);
-  unsigned long long mj = 0ull;
-  if (any && !diag && j < N)
-    for (int64_t bb = row_ptr[j]; bb < row_ptr[j + 1]; ++bb) {
-      const int64_t d = (int64_t)near_patch[bb] - P0I;
-      if (d >= 0 && d < 64) mj |= 1ull << d;
-    }
-  sMask[tid] = mj;
-  const float4 ta = srcA[i];
-  const float4 tb = kB ? srcB[i] : ta;
-  unsigned long long mi = 0ull;
-  if (any && i < N)
-    for (int64_t bb = row_ptr[i]; bb < row_ptr[i + 1]; ++bb) {
-      const int64_t d = (int64_t)near_patch[bb] - P0J;
-      if (d >= 0 && d < 64) mi |= 1ull << d;
-    }
-  const int lpi = (int)(i / np - P0I);
-  const bool pad_i = i >= N;
-  float acci[NO] = {0.f, 0.f, 0.f, 0.f};
+  // the targets i = I B + tid + t NTH: data, i-side masks, patch offsets
+  float4 ta[NT], tb[NT];
+  unsigned long long mi[NT];
+  int lpi[NT];
+  bool pad[NT];
+  float acci[NT][NO];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int64_t i = I * B + tid + t * NTH;
+    ta[t] = srcA[i];
+    tb[t] = kB ? srcB[i] : ta[t];
+    mi[t] = 0ull;
+    if (any && i < N)
+      for (int64_t bb = row_ptr[i]; bb < row_ptr[i + 1]; ++bb) {
+        const int64_t d = (int64_t)near_patch[bb] - P0J;
+        if (d >= 0 && d < 64) mi[t] |= 1ull << d;
+      }
+    lpi[t] = (int)(i / np - P0I);
+    pad[t] = i >= N;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acci[t][o] = 0.f;
+  }
   __syncthreads();
   const int up = (lane + 1) & 31;
   if (diag) {  // the target side only (padded targets lie in this block only)
     float none[NO] = {0.f, 0.f, 0.f, 0.f};
     for (int s = 0; s < B; ++s) {
       const int e = 64 * (s >> 5) + (s & 31);
-      const bool msk_i = pad_i || ((mi >> sLp[s]) & 1ull);
-      f32_pair_sym<KIND, true>(ta, tb, sA[e], kB ? sB[e] : sA[e], msk_i, true, acci, none);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const bool msk_i = pad[t] || ((mi[t] >> sLp[s]) & 1ull);
+        f32_pair_sym<KIND, true>(ta[t], tb[t], sA[e], kB ? sB[e] : sA[e], msk_i, true, acci[t], none);
+      }
     }
   } else {
     // 32 x 32 warp tiles: lane t takes source (t + k) mod 32 at step k; the
@@ -610,12 +630,22 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
         // lane t takes sources t + 2k and t + 2k + 1 at step k; its two
         // source-sum slots move two lanes down after each step, so that lane
         // t ends with source t in the low slot and source t + 1 in the high
-        const u64 T[6] = {pk2(ta.x, ta.x), pk2(ta.y, ta.y), pk2(ta.z, ta.z),
-                          pk2(tb.x, tb.x), pk2(tb.y, tb.y), pk2(tb.z, tb.z)};
-        const u64 QI1 = pk2(ta.w, ta.w), QI1N = pk2(-ta.w, -ta.w), QI2 = pk2(tb.w, tb.w);
+        u64 T[NT][6], QI1[NT], QI1N[NT], QI2[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          T[t][0] = pk2(ta[t].x, ta[t].x); T[t][1] = pk2(ta[t].y, ta[t].y); T[t][2] = pk2(ta[t].z, ta[t].z);
+          T[t][3] = pk2(tb[t].x, tb[t].x); T[t][4] = pk2(tb[t].y, tb[t].y); T[t][5] = pk2(tb[t].z, tb[t].z);
+          QI1[t] = pk2(ta[t].w, ta[t].w);
+          QI1N[t] = pk2(-ta[t].w, -ta[t].w);
+          QI2[t] = pk2(tb[t].w, tb[t].w);
+        }
         const u64 three = pk2(3.f, 3.f), mhalf = pk2(-0.5f, -0.5f);
         const int up2 = (lane + 2) & 31;
-        u64 ai[NO] = {0ull, 0ull, 0ull, 0ull}, aj[NO] = {0ull, 0ull, 0ull, 0ull};
+        u64 ai[NT][NO], aj[NO] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+#pragma unroll
+          for (int o = 0; o < NO; ++o) ai[t][o] = 0ull;
         const float4* q = &sP[0][64 * r + lane];
 #pragma unroll 4
         for (int k = 0; k < 16; ++k) {
@@ -626,7 +656,8 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
             S[2 * p] = pk2(v.x, v.y);
             S[2 * p + 1] = pk2(v.z, v.w);
           }
-          pair2_sym<KIND>(T, QI1, QI1N, QI2, S, ai, aj, three, mhalf);
+#pragma unroll
+          for (int t = 0; t < NT; ++t) pair2_sym<KIND>(T[t], QI1[t], QI1N[t], QI2[t], S, ai[t], aj, three, mhalf);
 #pragma unroll
           for (int o = 0; o < NO; ++o) aj[o] = shfl_u64(aj[o], up2);
         }
@@ -634,24 +665,35 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
 #pragma unroll
         for (int o = 0; o < NO; ++o) {
           float lo, hi;
-          upk2(ai[o], lo, hi);
-          acci[o] += lo + hi;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            upk2(ai[t][o], lo, hi);
+            acci[t][o] += lo + hi;
+          }
           upk2(aj[o], lo, hi);
           accj[o] = lo + __shfl_sync(0xffffffffu, hi, dn);  // source t: low slot here, high slot of lane t - 1
         }
       } else if (!any) {
 #pragma unroll 8
         for (int k = 0; k < 32; ++k) {
-          f32_pair_sym<KIND, false>(ta, tb, pa[k], pb[k], false, false, acci, accj);
+          const float4 a = pa[k], b = pb[k];
+#pragma unroll
+          for (int t = 0; t < NT; ++t) f32_pair_sym<KIND, false>(ta[t], tb[t], a, b, false, false, acci[t], accj);
 #pragma unroll
           for (int o = 0; o < NO; ++o) accj[o] = __shfl_sync(0xffffffffu, accj[o], up);
         }
       } else {
         for (int k = 0; k < 32; ++k) {
           const int s = 32 * r + ((lane + k) & 31);
-          const bool msk_i = (mi >> sLp[s]) & 1ull;
-          const bool msk_j = (sMask[s] >> lpi) & 1ull;
-          f32_pair_sym<KIND, true>(ta, tb, pa[k], pb[k], msk_i, msk_j, acci, accj);
+          const float4 a = pa[k], b = pb[k];
+          const int lp = sLp[s];
+          const unsigned long long ms = sMask[s];
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const bool msk_i = (mi[t] >> lp) & 1ull;
+            const bool msk_j = (ms >> lpi[t]) & 1ull;
+            f32_pair_sym<KIND, true>(ta[t], tb[t], a, b, msk_i, msk_j, acci[t], accj);
+          }
 #pragma unroll
           for (int o = 0; o < NO; ++o) accj[o] = __shfl_sync(0xffffffffu, accj[o], up);
         }
@@ -660,19 +702,28 @@ __global__ void __launch_bounds__(NTH) k_far32_sym(int64_t N, int np, const floa
       for (int o = 0; o < NO; ++o) sRed[warp][32 * r + lane][o] = accj[o];
     }
   }
-  if (!pad_i)
 #pragma unroll
-    for (int o = 0; o < NO; ++o) red_add_f64(out + o * N + i, (double)acci[o]);
+  for (int t = 0; t < NT; ++t) {
+    const int64_t i = I * B + tid + t * NTH;
+    if (!pad[t])
+#pragma unroll
+      for (int o = 0; o < NO; ++o) red_add_f64(out + o * N + i, (double)acci[t][o]);
+  }
   if (diag) return;
   __syncthreads();
-  if (j < N)
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    const int ls = tid + u * NTH;
+    const int64_t j = J * B + ls;
+    if (j >= N) continue;
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
       double v = 0.0;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) v += (double)sRed[w][tid][o];
+      for (int w = 0; w < NW; ++w) v += (double)sRed[w][ls][o];
       red_add_f64(out + o * N + j, v);
     }
+  }
 }
 
 // flag (target block, source tile) pairs that contain a near pair
@@ -774,9 +825,9 @@ static int launch_far32x2(lb_ctx* c, const void* srcA, const void* srcB, double*
 // natural register count (0), capped for three resident blocks per SM (1),
 // with 2 targets per thread (2).
 // the symmetric kernels (one float64 sum per accumulator: *ns = -1)
-template <int KIND, bool PACKED>
+template <int KIND, bool PACKED, int NT>
 static int launch_far32_sym(lb_ctx* c, const void* A, const void* B, double* part, int* ns) {
-  constexpr int NTH = 128;
+  constexpr int NTH = 128;  // nodes per block; the CTA has NTH / NT threads
   if (c->np * 62 < NTH) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
   if (c->Npad % NTH) return lb_fail(c, LB_EINVAL, "node padding is not a multiple of the block");
   MaskTable* m = nullptr;
@@ -786,7 +837,7 @@ static int launch_far32_sym(lb_ctx* c, const void* A, const void* B, double* par
   if (nblk > 0x7fffffffLL) return lb_fail(c, LB_EINVAL, "too many node blocks for one launch");
   LB_CUDA(c, cudaMemsetAsync(part, 0, 4 * c->N * sizeof(double), c->stream));
   ProfScope prof(c, LB_PROF_FAR32_K1 + KIND, c->N * c->N);
-  k_far32_sym<KIND, NTH, PACKED><<<(unsigned)nblk, NTH, 0, c->stream>>>(c->N, c->np, (const float4*)A, (const float4*)B,
+  k_far32_sym<KIND, PACKED, NT><<<(unsigned)nblk, NTH / NT, 0, c->stream>>>(c->N, c->np, (const float4*)A, (const float4*)B,
                                                                m->flags, m->ntiles, c->row_ptr, c->near_patch, part);
   LB_LAUNCH(c);
   lb_pair_counter += c->N * c->N;
@@ -795,15 +846,26 @@ static int launch_far32_sym(lb_ctx* c, const void* A, const void* B, double* par
 }
 
 // launch variants of the single-density float32 passes (chosen by timing):
-// 0-2 the tiled kernels below; K1 and K2 also 3, the symmetric kernel, and
-// 4, the same with the packed two-source loop
+// 0-2 the tiled kernels below; K1 and K2 also 3, the symmetric kernel, 4,
+// the same with the packed two-source loop, and 5 and 6, those two with two
+// targets per lane
 #define LB_FP32_VARIANTS 3
-static int fp32_nvariants(int kind) { return (kind == FAR_K1 || kind == FAR_K2) ? 5 : LB_FP32_VARIANTS; }
+static int fp32_nvariants(int kind) { return (kind == FAR_K1 || kind == FAR_K2) ? 7 : LB_FP32_VARIANTS; }
 static int launch_fp32(lb_ctx* c, int kind, int variant, const void* A, const void* B, double* part, int* ns) {
-  if (variant == 3 && kind == FAR_K1) return launch_far32_sym<FAR_K1, false>(c, A, B, part, ns);
-  if (variant == 3 && kind == FAR_K2) return launch_far32_sym<FAR_K2, false>(c, A, B, part, ns);
-  if (variant == 4 && kind == FAR_K1) return launch_far32_sym<FAR_K1, true>(c, A, B, part, ns);
-  if (variant == 4 && kind == FAR_K2) return launch_far32_sym<FAR_K2, true>(c, A, B, part, ns);
+  if (kind == FAR_K1 || kind == FAR_K2) {
+    const bool k1 = kind == FAR_K1;
+    switch (variant) {
+      case 3: return k1 ? launch_far32_sym<FAR_K1, false, 1>(c, A, B, part, ns)
+                        : launch_far32_sym<FAR_K2, false, 1>(c, A, B, part, ns);
+      case 4: return k1 ? launch_far32_sym<FAR_K1, true, 1>(c, A, B, part, ns)
+                        : launch_far32_sym<FAR_K2, true, 1>(c, A, B, part, ns);
+      case 5: return k1 ? launch_far32_sym<FAR_K1, false, 2>(c, A, B, part, ns)
+                        : launch_far32_sym<FAR_K2, false, 2>(c, A, B, part, ns);
+      case 6: return k1 ? launch_far32_sym<FAR_K1, true, 2>(c, A, B, part, ns)
+                        : launch_far32_sym<FAR_K2, true, 2>(c, A, B, part, ns);
+      default: break;
+    }
+  }
   switch (kind) {
     case FAR_K1:
       if (variant == 1) return launch_far32x2<FAR_K1, 4, 128, 128, 3>(c, A, B, part, ns);

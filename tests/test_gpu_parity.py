@@ -162,11 +162,11 @@ def test_operators(lb, name, form, prec):
 @pytest.mark.parametrize("name", CASES)
 def test_operators_fp32_every_variant(lb, name):
     """Every float32 launch variant against the oracle: A3 through K1 and K2
-    (variants 0-4, 3 and 4 the symmetric kernels), A2 through all-four and
+    (variants 0-6, 3 to 6 the symmetric kernels), A2 through all-four and
     K4 (0-2).  Float32 pairs: 2e-5 relative, as for the far sums."""
     rng = np.random.default_rng(25)
     tau = None
-    for form, kinds, nvar in (("A3", (0, 2), 5), ("A2", (1, 3), 3)):
+    for form, kinds, nvar in (("A3", (0, 2), 7), ("A2", (1, 3), 3)):
         ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3 if form == "A3" else lb.LB_A2,
                             precision=lb.LB_FP32)
         tau = rng.standard_normal((1, d.geo.N))
