@@ -115,6 +115,13 @@ class ClockSampler:
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+        # nvidia-smi's start-up (NVML initialisation) must not overlap the
+        # timed region: wait for its first sample line (at most 5 s)
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 5.0:
+            if self.proc.poll() is not None or os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
         time.sleep(0.3)
         return self
 

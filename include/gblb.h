@@ -361,8 +361,10 @@ int lb_geometry_gradient(lb_ctx* ctx, int nrhs, const double* f, const double* g
  * packed with 2 targets per thread; K1 and A3 pass 2 also 3: each unordered
  * node pair evaluated once for both directions, 4: the same with two
  * sources per packed instruction, 5 and 6: 3 and 4 with two targets per
- * thread), -1 = not tuned yet.
- * shapes: host memory of 12 ints. */
+ * thread), -1 = not tuned yet.  shapes[12], shapes[13]: the symmetric
+ * double-float kernels of A3 pass 1 and pass 2 (0: one target per thread,
+ * 1: two), -1 = not tuned yet.
+ * shapes: host memory of 14 ints. */
 int lb_get_tuning(lb_ctx* ctx, int* shapes);
 
 /* Far-field sums of one density that allocate nothing: the float32 pair
@@ -407,12 +409,14 @@ int lb_far_sums_noalloc(int64_t npatch, int np, const double* X, const double* n
  * lb_upload_geometry leaves no geometry (upload again). */
 int lb_debug_fail_alloc(lb_ctx* ctx, int64_t after);
 
-/* Launch variant of the single-density float32 passes for tests (not in the
- * paper): variant v (as reported in lb_get_tuning's shapes[8 + kind]) is
- * used for pass `kind` (0..3) on this context's surface from now on, in this
- * process, in place of the timed choice.  LB_EINVAL for a kind or variant out
- * of range (variants 3 to 6 exist for kinds 0 and 2 only); LB_ESTATE before a
- * geometry is uploaded. */
+/* Launch variant of a timed pass for tests (not in the paper): variant v is
+ * used for pass `kind` on this context's surface from now on, in this
+ * process, in place of the timed choice.  kind 0..3: the single-density
+ * float32 passes (variants as in lb_get_tuning's shapes[8 + kind]); 4, 5: the
+ * symmetric double-float kernels of A3 pass 1 and pass 2 (shapes[12],
+ * shapes[13]).  LB_EINVAL for a kind or variant out of range (float32
+ * variants 3 to 6 exist for kinds 0 and 2 only); LB_ESTATE before a geometry
+ * is uploaded. */
 int lb_debug_set_variant(lb_ctx* ctx, int kind, int variant);
 
 /* Surface divergence of tangential fields F [nrhs][N][3] -> out [nrhs][N]

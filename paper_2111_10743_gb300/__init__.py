@@ -210,9 +210,10 @@ class Context:
         self._check(_lib.lb_debug_fail_alloc(self._h, int(after)))
 
     def debug_set_variant(self, kind: int, variant: int):
-        """Use float32 launch variant `variant` for pass `kind` (0 K1, 1 all
-        four kernels, 2 A3 pass 2, 3 A2 pass 2) on this surface instead of
-        the timed choice (test hook)."""
+        """Use launch variant `variant` for pass `kind` on this surface
+        instead of the timed choice (test hook).  kind: float32 0 K1, 1 all
+        four kernels, 2 A3 pass 2, 3 A2 pass 2; double-float symmetric 4 K1,
+        5 A3 pass 2."""
         self._check(_lib.lb_debug_set_variant(self._h, int(kind), int(variant)))
 
     def set_profiling(self, on: bool = True):
@@ -220,7 +221,7 @@ class Context:
 
     def get_tuning(self) -> dict:
         """Launch shapes picked by the batched passes' tuner (-1: not tuned)."""
-        a = (ctypes.c_int * 12)()
+        a = (ctypes.c_int * 14)()
         self._check(_lib.lb_get_tuning(self._h, a))
         names = {0: "128x64", 1: "128x128", 2: "256x64", -1: None}
         out = {}
@@ -234,6 +235,9 @@ class Context:
         for kind, kn in enumerate(("k1", "kall", "k2", "k4")):
             v = a[8 + kind]
             out[f"far32_single_{kn}"] = single[kind][v] if v >= 0 else None
+        for p, kn in enumerate(("k1", "k2")):
+            v = a[12 + p]
+            out[f"fardf_sym_{kn}"] = ("nt1", "nt2")[v] if v >= 0 else None
         return out
 
     def get_profile(self) -> dict:

@@ -972,10 +972,13 @@ int lb_far_tuned_variant(lb_ctx* c, int kind) { return lb_tuned_choice(c, kind);
 extern "C" int lb_debug_set_variant(lb_ctx* c, int kind, int variant) {
   if (!c) return lb_fail(nullptr, LB_EINVAL, "null context");
   if (!c->have_geom) return lb_fail(c, LB_ESTATE, "no geometry uploaded");
-  if (kind < 0 || kind > 3 || variant < 0 || variant >= fp32_nvariants(kind))
-    return lb_fail(c, LB_EINVAL, "no float32 launch variant %d for pass kind %d", variant, kind);
+  // kinds 0..3: float32 passes; 4, 5: the symmetric double-float K1, K2
+  const int nvar = kind >= 0 && kind <= 3 ? fp32_nvariants(kind) : (kind == 4 || kind == 5 ? 2 : 0);
+  if (variant < 0 || variant >= nvar)
+    return lb_fail(c, LB_EINVAL, "no launch variant %d for pass kind %d", variant, kind);
+  const int key = kind <= 3 ? kind : LB_TUNE_DFSYM + (kind == 4 ? FAR_K1 : FAR_K2);
   std::lock_guard<std::mutex> lk(g_single_mu);
-  g_single[SingleKey{c->device, c->N, c->np, kind}] = variant;
+  g_single[SingleKey{c->device, c->N, c->np, key}] = variant;
   return LB_OK;
 }
 

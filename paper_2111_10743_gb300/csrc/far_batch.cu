@@ -744,5 +744,7 @@ extern "C" int lb_get_tuning(lb_ctx* c, int* shapes) {
         shapes[p * 4 + k * 2 + r] = it == g_tune.end() ? -1 : it->second;
       }
   for (int kind = 0; kind < 4; ++kind) shapes[8 + kind] = lb_far_tuned_variant(c, kind);
+  shapes[12] = lb_tuned_choice(c, LB_TUNE_DFSYM + FAR_K1);
+  shapes[13] = lb_tuned_choice(c, LB_TUNE_DFSYM + FAR_K2);
   return LB_OK;
 }

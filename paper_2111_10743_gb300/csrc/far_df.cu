@@ -318,12 +318,14 @@ __device__ __forceinline__ void df_pair_sym(const float* t, const float4& A, con
   df_acc(accj[3], df_mul(df_mul(F2{-q2i.h, -q2i.l}, rinv3), kkj));
 }
 
-template <int KIND, int NTH>
-__global__ void __launch_bounds__(NTH) k_far_df_sym(int64_t N, int np, int nb, const float4* __restrict__ S,
-                                                    int64_t Npad, const uint8_t* __restrict__ flags, int64_t ntiles,
-                                                    const int64_t* __restrict__ row_ptr,
-                                                    const int32_t* __restrict__ near_patch, double* __restrict__ out) {
-  constexpr int NO = 4, NW = NTH / 32, B = NTH;
+// NT: targets per lane (the CTA has 128 / NT threads for a 128-node block)
+template <int KIND, int NT>
+__global__ void __launch_bounds__(128 / NT) k_far_df_sym(int64_t N, int np, int nb, const float4* __restrict__ S,
+                                                         int64_t Npad, const uint8_t* __restrict__ flags,
+                                                         int64_t ntiles, const int64_t* __restrict__ row_ptr,
+                                                         const int32_t* __restrict__ near_patch,
+                                                         double* __restrict__ out) {
+  constexpr int NO = 4, B = 128, NTH = B / NT, NW = NTH / 32;
   __shared__ float4 sA[B], sB[B], sC[B], sD[B];
   __shared__ unsigned long long sMask[B];
   __shared__ int sLp[B];
@@ -332,50 +334,62 @@ __global__ void __launch_bounds__(NTH) k_far_df_sym(int64_t N, int np, int nb, c
   tri_pair(blockIdx.x, I, J);
   const bool diag = I == J;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t i = I * B + tid, j = J * B + tid;
   const int64_t P0I = (I * B) / np, P0J = (J * B) / np;
   const bool any = flags[I * ntiles + J] != 0 || flags[J * ntiles + I] != 0;
   // stage block J with its j-side masks (bit p: patch P0I + p in Near(j))
-  sA[tid] = S[j];
-  sB[tid] = S[Npad + j];
-  sC[tid] = S[2 * Npad + j];
-  sD[tid] = S[3 * Npad + j];
-  sLp[tid] = (int)(j / np - P0J);
-  unsigned long long mj = 0ull;
-  if (any && !diag && j < N)
-    for (int64_t bb = row_ptr[j]; bb < row_ptr[j + 1]; ++bb) {
-      const int64_t d = (int64_t)near_patch[bb] - P0I;
-      if (d >= 0 && d < 64) mj |= 1ull << d;
-    }
-  sMask[tid] = mj;
-  // the target: data, i-side mask over block J's patches, patch offset
-  float tv[16];
-  {
-    const float4 a = S[i], b = S[Npad + i], c = S[2 * Npad + i], d = S[3 * Npad + i];
-    tv[0] = a.x; tv[1] = a.y; tv[2] = a.z;
-    tv[3] = b.x; tv[4] = b.y; tv[5] = b.z;
-    tv[6] = c.x; tv[7] = c.y; tv[8] = c.z;
-    tv[9] = d.x; tv[10] = d.y; tv[11] = d.z;
-    tv[12] = a.w; tv[13] = b.w; tv[14] = c.w; tv[15] = d.w;
-  }
-  unsigned long long mi = 0ull;
-  if (any && i < N)
-    for (int64_t bb = row_ptr[i]; bb < row_ptr[i + 1]; ++bb) {
-      const int64_t d = (int64_t)near_patch[bb] - P0J;
-      if (d >= 0 && d < 64) mi |= 1ull << d;
-    }
-  const int lpi = (int)(i / np - P0I);
-  const bool pad_i = i >= N;
-  F2 acci[NO];
 #pragma unroll
-  for (int o = 0; o < NO; ++o) acci[o] = {0.f, 0.f};
+  for (int u = 0; u < NT; ++u) {
+    const int ls = tid + u * NTH;
+    const int64_t j = J * B + ls;
+    sA[ls] = S[j];
+    sB[ls] = S[Npad + j];
+    sC[ls] = S[2 * Npad + j];
+    sD[ls] = S[3 * Npad + j];
+    sLp[ls] = (int)(j / np - P0J);
+    unsigned long long mj = 0ull;
+    if (any && !diag && j < N)
+      for (int64_t bb = row_ptr[j]; bb < row_ptr[j + 1]; ++bb) {
+        const int64_t d = (int64_t)near_patch[bb] - P0I;
+        if (d >= 0 && d < 64) mj |= 1ull << d;
+      }
+    sMask[ls] = mj;
+  }
+  // the targets i = I B + tid + t NTH: data, i-side masks over block J's
+  // patches, patch offsets
+  float tv[NT][16];
+  unsigned long long mi[NT];
+  int lpi[NT];
+  bool pad[NT];
+  F2 acci[NT][NO];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const int64_t i = I * B + tid + t * NTH;
+    const float4 a = S[i], b = S[Npad + i], c = S[2 * Npad + i], d = S[3 * Npad + i];
+    tv[t][0] = a.x; tv[t][1] = a.y; tv[t][2] = a.z;
+    tv[t][3] = b.x; tv[t][4] = b.y; tv[t][5] = b.z;
+    tv[t][6] = c.x; tv[t][7] = c.y; tv[t][8] = c.z;
+    tv[t][9] = d.x; tv[t][10] = d.y; tv[t][11] = d.z;
+    tv[t][12] = a.w; tv[t][13] = b.w; tv[t][14] = c.w; tv[t][15] = d.w;
+    mi[t] = 0ull;
+    if (any && i < N)
+      for (int64_t bb = row_ptr[i]; bb < row_ptr[i + 1]; ++bb) {
+        const int64_t dd = (int64_t)near_patch[bb] - P0J;
+        if (dd >= 0 && dd < 64) mi[t] |= 1ull << dd;
+      }
+    lpi[t] = (int)(i / np - P0I);
+    pad[t] = i >= N;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) acci[t][o] = {0.f, 0.f};
+  }
   __syncthreads();
   if (diag) {  // the target side only, every source of the block in turn
     F2 none[NO] = {};  // j-side sums of the diagonal: charges masked, never read
-    for (int s = 0; s < B; ++s) {
-      const bool msk_i = pad_i || ((mi >> sLp[s]) & 1ull);
-      df_pair_sym<KIND>(tv, sA[s], sB[s], sC[s], sD[s], msk_i, true, acci, none);
-    }
+    for (int s = 0; s < B; ++s)
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const bool msk_i = pad[t] || ((mi[t] >> sLp[s]) & 1ull);
+        df_pair_sym<KIND>(tv[t], sA[s], sB[s], sC[s], sD[s], msk_i, true, acci[t], none);
+      }
   } else {
     // 32 x 32 warp tiles: at step k lane t takes source (t + k) mod 32 of the
     // tile, and the source-side sums move one lane down after each step, so
@@ -389,16 +403,24 @@ __global__ void __launch_bounds__(NTH) k_far_df_sym(int64_t N, int np, int nb, c
 #pragma unroll 2
         for (int k = 0; k < 32; ++k) {
           const int s = 32 * r + ((lane + k) & 31);
-          df_pair_sym<KIND, false>(tv, sA[s], sB[s], sC[s], sD[s], false, false, acci, accj);
+          const float4 a = sA[s], b = sB[s], c = sC[s], d = sD[s];
+#pragma unroll
+          for (int t = 0; t < NT; ++t) df_pair_sym<KIND, false>(tv[t], a, b, c, d, false, false, acci[t], accj);
 #pragma unroll
           for (int o = 0; o < NO; ++o) accj[o] = shfl_idx_v(accj[o], (lane + 1) & 31);
         }
       } else {
         for (int k = 0; k < 32; ++k) {
           const int s = 32 * r + ((lane + k) & 31);
-          const bool msk_i = (mi >> sLp[s]) & 1ull;
-          const bool msk_j = (sMask[s] >> lpi) & 1ull;
-          df_pair_sym<KIND>(tv, sA[s], sB[s], sC[s], sD[s], msk_i, msk_j, acci, accj);
+          const float4 a = sA[s], b = sB[s], c = sC[s], d = sD[s];
+          const int lp = sLp[s];
+          const unsigned long long ms = sMask[s];
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const bool msk_i = (mi[t] >> lp) & 1ull;
+            const bool msk_j = (ms >> lpi[t]) & 1ull;
+            df_pair_sym<KIND>(tv[t], a, b, c, d, msk_i, msk_j, acci[t], accj);
+          }
 #pragma unroll
           for (int o = 0; o < NO; ++o) accj[o] = shfl_idx_v(accj[o], (lane + 1) & 31);
         }
@@ -407,24 +429,33 @@ __global__ void __launch_bounds__(NTH) k_far_df_sym(int64_t N, int np, int nb, c
       for (int o = 0; o < NO; ++o) sRed[warp][32 * r + lane][o] = accj[o];
     }
   }
-  if (!pad_i)
 #pragma unroll
-    for (int o = 0; o < NO; ++o) red_add_f64(out + o * N + i, df_to_double(acci[o]));
+  for (int t = 0; t < NT; ++t) {
+    const int64_t i = I * B + tid + t * NTH;
+    if (!pad[t])
+#pragma unroll
+      for (int o = 0; o < NO; ++o) red_add_f64(out + o * N + i, df_to_double(acci[t][o]));
+  }
   if (diag) return;
   __syncthreads();
-  if (j < N)
+#pragma unroll
+  for (int u = 0; u < NT; ++u) {
+    const int ls = tid + u * NTH;
+    const int64_t j = J * B + ls;
+    if (j >= N) continue;
 #pragma unroll
     for (int o = 0; o < NO; ++o) {
-      F2 v = sRed[0][tid][o];
+      F2 v = sRed[0][ls][o];
 #pragma unroll
-      for (int w = 1; w < NW; ++w) v = df_add(v, sRed[w][tid][o]);
+      for (int w = 1; w < NW; ++w) v = df_add(v, sRed[w][ls][o]);
       red_add_f64(out + o * N + j, df_to_double(v));
     }
+  }
 }
 
-template <int KIND>
+template <int KIND, int NT>
 static int launch_df_sym(lb_ctx* c, const void* S, double* part) {
-  constexpr int NTH = 128, B = NTH;
+  constexpr int B = 128;
   if (c->np * 62 < B) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
   if (c->Npad % B) return lb_fail(c, LB_EINVAL, "node padding is not a multiple of the block");
   MaskTable* m = nullptr;
@@ -435,17 +466,35 @@ static int launch_df_sym(lb_ctx* c, const void* S, double* part) {
   LB_CUDA(c, cudaMemsetAsync(part, 0, 4 * c->N * sizeof(double), c->stream));
   const int64_t pairs = c->N * c->N;
   ProfScope prof(c, LB_PROF_FARDF_K1 + KIND, pairs);
-  k_far_df_sym<KIND, NTH><<<(unsigned)nblk, NTH, 0, c->stream>>>(c->N, c->np, (int)nb, (const float4*)S, c->Npad,
-                                                                m->flags, m->ntiles, c->row_ptr, c->near_patch, part);
+  k_far_df_sym<KIND, NT><<<(unsigned)nblk, B / NT, 0, c->stream>>>(c->N, c->np, (int)nb, (const float4*)S, c->Npad,
+                                                                  m->flags, m->ntiles, c->row_ptr, c->near_patch,
+                                                                  part);
   LB_LAUNCH(c);
   lb_pair_counter += pairs;
   return LB_OK;
 }
 
+struct DfSymLaunch {
+  int kind;
+  const void* S;
+  double* part;
+};
+// variant 0: one target per lane, 1: two
+static int df_sym_cb(lb_ctx* c, int v, void* arg) {
+  const DfSymLaunch* a = (const DfSymLaunch*)arg;
+  if (a->kind == FAR_K1)
+    return v == 0 ? launch_df_sym<FAR_K1, 1>(c, a->S, a->part) : launch_df_sym<FAR_K1, 2>(c, a->S, a->part);
+  return v == 0 ? launch_df_sym<FAR_K2, 1>(c, a->S, a->part) : launch_df_sym<FAR_K2, 2>(c, a->S, a->part);
+}
+
 int lb_far_launch_df(lb_ctx* c, int kind, const void* S, double* part, int* nsplit) {
   if ((kind == FAR_K1 || kind == FAR_K2) && !c->far_order) {
     *nsplit = -1;
-    return kind == FAR_K1 ? launch_df_sym<FAR_K1>(c, S, part) : launch_df_sym<FAR_K2>(c, S, part);
+    // one or two targets per lane, timed on first use
+    DfSymLaunch a{kind, S, part};
+    int v = 0;
+    LB_CHECK(lb_tune_choice(c, LB_TUNE_DFSYM + kind, 2, df_sym_cb, &a, &v));
+    return df_sym_cb(c, v, &a);
   }
   switch (kind) {
     case FAR_K1: return launch_df_t<FAR_K1>(c, S, part, nsplit);

@@ -266,7 +266,9 @@ int lb_far_tuned_variant(lb_ctx* c, int kind);
 // arg) runs variant v): each is launched twice, the second timed, once per
 // (device, N, n_p, key_kind) and process; the fastest is kept.  Variant 0
 // while a graph is being captured and nothing is tuned yet.  key_kind 0..3:
-// the float32 single-density kinds.
+// the float32 single-density kinds; LB_TUNE_DFSYM + kind: the symmetric
+// double-float kernels.
+#define LB_TUNE_DFSYM 8
 int lb_tune_choice(lb_ctx* c, int key_kind, int nvar, int (*launch)(lb_ctx*, int, void*), void* arg, int* choice);
 // the choice made for key_kind, -1 if not tuned yet
 int lb_tuned_choice(lb_ctx* c, int key_kind);

@@ -181,6 +181,22 @@ def test_operators_fp32_every_variant(lb, name):
         ctx.close()
 
 
+@pytest.mark.parametrize("name", CASES)
+def test_operator_df64_every_variant(lb, name):
+    """Both launch variants of the symmetric double-float A3 passes (one or
+    two targets per thread) against the oracle at 1e-12."""
+    ctx, s, d = ctx_for(lb, name, formulation=lb.LB_A3, precision=lb.LB_DF64)
+    tau = np.random.default_rng(26).standard_normal((1, d.geo.N))
+    ref = d.apply("A3", tau)
+    for v in range(2):
+        ctx.debug_set_variant(4, v)
+        ctx.debug_set_variant(5, v)
+        assert _rel(ctx.apply_A(tau), ref) < 1e-12, v
+    with pytest.raises(lb.LBError):
+        ctx.debug_set_variant(5, 2)
+    ctx.close()
+
+
 @pytest.mark.parametrize("name", ["sphere300", "torus1920"])
 @pytest.mark.parametrize("form", ["A3", "A2"])
 @pytest.mark.parametrize("prec", ["fp64", "df64"])
