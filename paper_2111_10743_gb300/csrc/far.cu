@@ -516,9 +516,10 @@ __device__ __forceinline__ u64 shfl_u64(u64 v, int src) {
 }
 
 // NT: targets per lane (the CTA has 128 / NT threads for a 128-node block),
-// so that each source load and each rotation step serves NT pairs
-template <int KIND, bool PACKED, int NT>
-__global__ void __launch_bounds__(128 / NT) k_far32_sym(int64_t N, int np, const float4* __restrict__ srcA,
+// so that each source load and each rotation step serves NT pairs; MINB:
+// resident blocks per SM asked of ptxas (0: unspecified)
+template <int KIND, bool PACKED, int NT, int MINB = 0>
+__global__ void __launch_bounds__(128 / NT, MINB) k_far32_sym(int64_t N, int np, const float4* __restrict__ srcA,
                                                         const float4* __restrict__ srcB,
                                                         const uint8_t* __restrict__ flags, int64_t ntiles,
                                                         const int64_t* __restrict__ row_ptr,
@@ -526,16 +527,19 @@ __global__ void __launch_bounds__(128 / NT) k_far32_sym(int64_t N, int np, const
                                                         double* __restrict__ out) {
   constexpr int NO = 4, B = 128, NTH = B / NT, NW = NTH / 32;
   constexpr bool kB = KIND != FAR_K1;
-  // each 32-source tile stored twice over (64 entries), so that lane t reads
-  // source (t + k) mod 32 of tile r at entry 64 r + t + k: a per-lane base
-  // address plus the step as an immediate offset
-  __shared__ float4 sA[2 * B], sB[kB ? 2 * B : 1];
+  // scalar loop: each 32-source tile stored twice over (64 entries), so that
+  // lane t reads source (t + k) mod 32 of tile r at entry 64 r + t + k: a
+  // per-lane base address plus the step as an immediate offset.  The packed
+  // forms read these tiles only in the masked and diagonal loops and keep
+  // one copy (entry 32 r + (t + k) mod 32), which saves the shared memory
+  // that bounds their resident blocks.
+  constexpr int DUP = PACKED ? 1 : 2;
+  __shared__ float4 sA[DUP * B], sB[kB ? DUP * B : 1];
   // packed loop: the same tiles pair-interleaved, entry e of tile r holding
-  // (c_e, c_(e+1)) for two components c per plane, sources e and e + 1 mod
-  // 32 (planes: x y, z q1, n_x n_y, n_z q2), so that one 16-byte load gives
-  // two packed operands
+  // (c_e, c_(e+1 mod 32)) for two components c per plane (planes: x y, z q1,
+  // n_x n_y, n_z q2), so that one 16-byte load gives two packed operands
   constexpr int NPL = PACKED ? (kB ? 4 : 2) : 1;
-  __shared__ float4 sP[NPL][PACKED ? 2 * B : 1];
+  __shared__ float4 sP[NPL][PACKED ? B : 1];
   __shared__ unsigned long long sMask[B];
   __shared__ int sLp[B];
   __shared__ float sRed[NW][B][NO];
@@ -549,31 +553,28 @@ __global__ void __launch_bounds__(128 / NT) k_far32_sym(int64_t N, int np, const
   for (int u = 0; u < NT; ++u) {  // stage block J: this thread's sources ls = tid + u NTH
     const int ls = tid + u * NTH, rt = ls >> 5;
     const int64_t j = J * B + ls;
-    const int e = 64 * rt + lane;
+    const int e = 32 * DUP * rt + lane;
     const float4 va = srcA[j];
     const float4 vb = kB ? srcB[j] : va;
     sA[e] = va;
-    sA[e + 32] = va;
+    if (!PACKED) sA[e + 32] = va;
     if (kB) {
       sB[e] = vb;
-      sB[e + 32] = vb;
+      if (!PACKED) sB[e + 32] = vb;
     }
     if (PACKED) {
-      // this source is the first element of entries lane, lane + 32 and the
-      // second of entries lane - 1 (mod 64) and lane + 31 of its tile
+      // this source is the first element of entry lane and the second of
+      // entry lane - 1 (mod 32) of its tile
       const float c[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-      const int f0 = 64 * rt + lane, f1 = f0 + 32;
-      const int g0 = 64 * rt + ((lane + 63) & 63), g1 = 64 * rt + lane + 31;
+      const int f0 = 32 * rt + lane, g0 = 32 * rt + ((lane + 31) & 31);
 #pragma unroll
       for (int p = 0; p < NPL; ++p) {
         float* a0 = reinterpret_cast<float*>(&sP[p][f0]);
-        float* a1 = reinterpret_cast<float*>(&sP[p][f1]);
         float* b0 = reinterpret_cast<float*>(&sP[p][g0]);
-        float* b1 = reinterpret_cast<float*>(&sP[p][g1]);
-        a0[0] = a1[0] = c[2 * p];
-        a0[2] = a1[2] = c[2 * p + 1];
-        b0[1] = b1[1] = c[2 * p];
-        b0[3] = b1[3] = c[2 * p + 1];
+        a0[0] = c[2 * p];
+        a0[2] = c[2 * p + 1];
+        b0[1] = c[2 * p];
+        b0[3] = c[2 * p + 1];
       }
     }
     sLp[ls] = (int)(j / np - P0J);
@@ -612,7 +613,7 @@ __global__ void __launch_bounds__(128 / NT) k_far32_sym(int64_t N, int np, const
   if (diag) {  // the target side only (padded targets lie in this block only)
     float none[NO] = {0.f, 0.f, 0.f, 0.f};
     for (int s = 0; s < B; ++s) {
-      const int e = 64 * (s >> 5) + (s & 31);
+      const int e = 32 * DUP * (s >> 5) + (s & 31);
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         const bool msk_i = pad[t] || ((mi[t] >> sLp[s]) & 1ull);
@@ -624,8 +625,8 @@ __global__ void __launch_bounds__(128 / NT) k_far32_sym(int64_t N, int np, const
     // source sums move one lane down after each step
     for (int r = 0; r < B / 32; ++r) {
       float accj[NO] = {0.f, 0.f, 0.f, 0.f};
-      const float4* pa = sA + 64 * r + lane;
-      const float4* pb = kB ? sB + 64 * r + lane : pa;
+      const float4* pa = sA + 32 * DUP * r;
+      const float4* pb = kB ? sB + 32 * DUP * r : pa;
       if (!any && PACKED) {
         // lane t takes sources t + 2k and t + 2k + 1 at step k; its two
         // source-sum slots move two lanes down after each step, so that lane
@@ -646,13 +647,14 @@ __global__ void __launch_bounds__(128 / NT) k_far32_sym(int64_t N, int np, const
         for (int t = 0; t < NT; ++t)
 #pragma unroll
           for (int o = 0; o < NO; ++o) ai[t][o] = 0ull;
-        const float4* q = &sP[0][64 * r + lane];
+        const float4* q = &sP[0][32 * r];
 #pragma unroll 4
         for (int k = 0; k < 16; ++k) {
+          const int e = (lane + 2 * k) & 31;
           u64 S[8];
 #pragma unroll
           for (int p = 0; p < NPL; ++p) {
-            const float4 v = q[p * 2 * B + 2 * k];
+            const float4 v = q[p * B + e];
             S[2 * p] = pk2(v.x, v.y);
             S[2 * p + 1] = pk2(v.z, v.w);
           }
@@ -673,10 +675,10 @@ __global__ void __launch_bounds__(128 / NT) k_far32_sym(int64_t N, int np, const
           upk2(aj[o], lo, hi);
           accj[o] = lo + __shfl_sync(0xffffffffu, hi, dn);  // source t: low slot here, high slot of lane t - 1
         }
-      } else if (!any) {
+      } else if (!PACKED && !any) {
 #pragma unroll 8
         for (int k = 0; k < 32; ++k) {
-          const float4 a = pa[k], b = pb[k];
+          const float4 a = pa[lane + k], b = pb[lane + k];  // (scalar form: DUP = 2)
 #pragma unroll
           for (int t = 0; t < NT; ++t) f32_pair_sym<KIND, false>(ta[t], tb[t], a, b, false, false, acci[t], accj);
 #pragma unroll
@@ -685,7 +687,8 @@ __global__ void __launch_bounds__(128 / NT) k_far32_sym(int64_t N, int np, const
       } else {
         for (int k = 0; k < 32; ++k) {
           const int s = 32 * r + ((lane + k) & 31);
-          const float4 a = pa[k], b = pb[k];
+          const int e = PACKED ? ((lane + k) & 31) : lane + k;
+          const float4 a = pa[e], b = pb[e];
           const int lp = sLp[s];
           const unsigned long long ms = sMask[s];
 #pragma unroll
@@ -825,7 +828,7 @@ static int launch_far32x2(lb_ctx* c, const void* srcA, const void* srcB, double*
 // natural register count (0), capped for three resident blocks per SM (1),
 // with 2 targets per thread (2).
 // the symmetric kernels (one float64 sum per accumulator: *ns = -1)
-template <int KIND, bool PACKED, int NT>
+template <int KIND, bool PACKED, int NT, int MINB = 0>
 static int launch_far32_sym(lb_ctx* c, const void* A, const void* B, double* part, int* ns) {
   constexpr int NTH = 128;  // nodes per block; the CTA has NTH / NT threads
   if (c->np * 62 < NTH) return lb_fail(c, LB_EINVAL, "patch too small for the source tile");
@@ -837,7 +840,7 @@ static int launch_far32_sym(lb_ctx* c, const void* A, const void* B, double* par
   if (nblk > 0x7fffffffLL) return lb_fail(c, LB_EINVAL, "too many node blocks for one launch");
   LB_CUDA(c, cudaMemsetAsync(part, 0, 4 * c->N * sizeof(double), c->stream));
   ProfScope prof(c, LB_PROF_FAR32_K1 + KIND, c->N * c->N);
-  k_far32_sym<KIND, PACKED, NT><<<(unsigned)nblk, NTH / NT, 0, c->stream>>>(c->N, c->np, (const float4*)A, (const float4*)B,
+  k_far32_sym<KIND, PACKED, NT, MINB><<<(unsigned)nblk, NTH / NT, 0, c->stream>>>(c->N, c->np, (const float4*)A, (const float4*)B,
                                                                m->flags, m->ntiles, c->row_ptr, c->near_patch, part);
   LB_LAUNCH(c);
   lb_pair_counter += c->N * c->N;
@@ -1056,6 +1059,7 @@ struct EpiSpec {
   double scale[4];       // multiplies the far accumulator
   int kern[4];           // correction kernel (LB_K_*), or -1 for none
   const double* dens[4]; // density of the correction sum (float64)
+  int64_t kplane;        // float4 vectors per kernel plane of the float weight copies (nnzb * npv)
   const float* dh[4];    // its float32 copy / double-float hi part
   const float* dl[4];    // its double-float lo part
   double* out[4];        // [N]
@@ -1074,7 +1078,8 @@ __device__ __forceinline__ double to_d(F2 v) { return df_to_double(v); }
 // The float copies are padded to npv float4 vectors per (block, kernel) and
 // per patch (lb_lowp_vals, lowp_dens: zeros past np), so that every lane
 // moves four nodes' weights and densities with single 16-byte loads; the
-// rows are streamed, four vectors per lane in flight.
+// weights are kernel-major (plane k at k * sp.kplane vectors), so that a
+// row's blocks of one kernel are contiguous; four vectors per lane in flight.
 template <int MODE>
 __global__ void k_epilogue(int64_t N, int np, int npv, int nsplit, int nacc, const double* __restrict__ part,
                            const double* __restrict__ nrm, const int64_t* __restrict__ row_ptr,
@@ -1099,7 +1104,7 @@ __global__ void k_epilogue(int64_t N, int np, int npv, int nsplit, int nacc, con
         const int e = e0 + 32 * u;
         const int bl = e < tot ? e / npv : 0;
         const int qv = e < tot ? e - bl * npv : 0;
-        bq[u] = (rb + bl) * (LB_NKERNELS * (int64_t)npv) + qv;        // weights of kernel 0
+        bq[u] = (rb + bl) * (int64_t)npv + qv;                        // weights, kernel plane 0
         pq[u] = e < tot ? (int64_t)near_patch[rb + bl] * npv + qv : -1;  // densities
       }
 #pragma unroll
@@ -1108,7 +1113,7 @@ __global__ void k_epilogue(int64_t N, int np, int npv, int nsplit, int nacc, con
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
           if (o >= sp.nout || sp.kern[o] < 0) continue;
-          const int64_t wi = bq[u] + sp.kern[o] * (int64_t)npv;
+          const int64_t wi = bq[u] + sp.kern[o] * sp.kplane;
           const float4 w = __ldg(vh + wi);
           const float4 x = __ldg(reinterpret_cast<const float4*>(sp.dh[o]) + pq[u]);
           if constexpr (MODE == 1) {
@@ -1262,15 +1267,36 @@ static int split_pad(lb_ctx* c, int64_t nrows, const double* x, float* hi, float
   return LB_OK;
 }
 
-// float32 hi / lo copies of the correction weights, [nnzb][4][npp] with the
-// node index padded to a multiple of four, made on first use after the
-// corrections were loaded or built
+// hi / lo float copies of vals [nnzb][4][np] in kernel-major planes
+// [4][nnzb][npp] (rows padded with zeros to npp)
+__global__ void k_split_kmajor(int64_t nnzb, int np, int npp, const double* __restrict__ vals,
+                               float* __restrict__ hi, float* __restrict__ lo) {
+  const int64_t plane = nnzb * npp, n = LB_NKERNELS * plane;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / plane, rem = t - k * plane;
+    const int64_t b = rem / npp;
+    const int q = (int)(rem - b * npp);
+    const double v = q < np ? vals[(b * LB_NKERNELS + k) * np + q] : 0.0;
+    const float h = (float)v;
+    hi[t] = h;
+    lo[t] = (float)(v - (double)h);
+  }
+}
+
+// float32 hi / lo copies of the correction weights, kernel-major
+// [4][nnzb][npp] with the node index padded to a multiple of four, made on
+// first use after the corrections were loaded or built: a pass reads each
+// of its kernels' weights as one contiguous stream
 int lb_lowp_vals(lb_ctx* c) {
   if (!c->have_corr || c->vals_hi) return LB_OK;
-  const int64_t n = c->nnzb * LB_NKERNELS * lb_np_pad(c->np);
+  const int npp = lb_np_pad(c->np);
+  const int64_t n = c->nnzb * LB_NKERNELS * npp;
   LB_CHECK(lb_alloc(c, &c->vals_hi, (size_t)n));
   LB_CHECK(lb_alloc(c, &c->vals_lo, (size_t)n));
-  return split_pad(c, c->nnzb * LB_NKERNELS, c->vals, c->vals_hi, c->vals_lo);
+  const unsigned nb = (unsigned)std::min<int64_t>(8LL * c->sm_count, std::max<int64_t>(1, lb_div_up(n, 256)));
+  k_split_kmajor<<<nb, 256, 0, c->stream>>>(c->nnzb, c->np, npp, c->vals, c->vals_hi, c->vals_lo);
+  LB_LAUNCH(c);
+  return LB_OK;
 }
 
 // float32 / double-float copies of the distinct correction densities of sp,
@@ -1308,6 +1334,7 @@ static int run_epilogue(lb_ctx* c, int prec, int nsplit, int nacc, const double*
   const int npv = lb_np_pad(c->np) / 4;
   const float4* vh = corr ? (const float4*)c->vals_hi : nullptr;
   const float4* vl = corr ? (const float4*)c->vals_lo : nullptr;
+  sp.kplane = c->nnzb * (int64_t)npv;
   if (mode == 0)
     k_epilogue<0><<<grid, 256, 0, c->stream>>>(c->N, c->np, npv, nsplit, nacc, part, c->nrm, c->row_ptr,
                                                c->near_patch, corr ? c->vals : nullptr, nullptr, nullptr, sp);

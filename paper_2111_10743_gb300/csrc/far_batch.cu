@@ -317,7 +317,7 @@ __global__ void k_packqdf(int64_t N, int64_t Npad, int R, int RC, int npl, const
 //   pass 1: mu1 = S' tau (out0), mu2 = S tau (out1)
 //   pass 2: S' mu1, S mu2, S' mu2, (S''+D') mu2 (out0..out3)
 template <int RC, bool PASS2, int MODE>
-__global__ void k_epib(int64_t N, int np, int R, int nsplit, const double* __restrict__ part,
+__global__ void k_epib(int64_t N, int np, int64_t nnzb, int R, int nsplit, const double* __restrict__ part,
                        const double* __restrict__ nrm, const int64_t* __restrict__ row_ptr,
                        const int32_t* __restrict__ near_patch, const float4* __restrict__ vh,
                        const float4* __restrict__ vl, const float4* __restrict__ D, double* __restrict__ out0,
@@ -337,18 +337,19 @@ __global__ void k_epib(int64_t N, int np, int R, int nsplit, const double* __res
   for (int k = 0; k < V; ++k) cs[k] = T{};
   // the row's (block, node) pairs flattened; each lane walks them 32 apart,
   // so that a warp reads 32 consecutive nodes' densities per load; the float
-  // weights are stored [block][kernel][npp], npp = np rounded up to four
+  // weights are stored kernel-major [kernel][block][npp], npp = np rounded up
+  // to four, so that a warp's weights of one kernel are contiguous
   const int npp = (np + 3) & ~3;
   const int64_t rb = row_ptr[i];
   const int ne = (int)((row_ptr[i + 1] - rb) * np);
-  const int64_t stride = LB_NKERNELS * (int64_t)npp;
+  const int64_t kp = nnzb * (int64_t)npp;  // floats per kernel plane
   int bo = lane / np, q = lane - (lane / np) * np;
   const float* vhf = reinterpret_cast<const float*>(vh);
   const float* vlf = reinterpret_cast<const float*>(vl);
   for (int e = lane; e < ne; e += 32) {
     const int64_t b = rb + bo;
     const int64_t col = (int64_t)near_patch[b] * np + q;
-    const int64_t wo = b * stride + q;
+    const int64_t wo = b * npp + q;
     float dv[NF4 * 4];
 #pragma unroll
     for (int g = 0; g < NF4; ++g) {
@@ -356,8 +357,8 @@ __global__ void k_epib(int64_t N, int np, int R, int nsplit, const double* __res
       dv[4 * g] = v.x; dv[4 * g + 1] = v.y; dv[4 * g + 2] = v.z; dv[4 * g + 3] = v.w;
     }
     if constexpr (MODE == 1) {
-      const float wS = __ldg(vhf + wo + LB_K_S * npp), wSp = __ldg(vhf + wo + LB_K_SP * npp);
-      const float wSD = PASS2 ? __ldg(vhf + wo + LB_K_SPPDP * npp) : 0.f;
+      const float wS = __ldg(vhf + wo + LB_K_S * kp), wSp = __ldg(vhf + wo + LB_K_SP * kp);
+      const float wSD = PASS2 ? __ldg(vhf + wo + LB_K_SPPDP * kp) : 0.f;
       float* c = cs;
 #pragma unroll
       for (int r = 0; r < RC; ++r) {
@@ -374,10 +375,10 @@ __global__ void k_epib(int64_t N, int np, int R, int nsplit, const double* __res
         }
       }
     } else {
-      const F2 wS = {__ldg(vhf + wo + LB_K_S * npp), __ldg(vlf + wo + LB_K_S * npp)};
-      const F2 wSp = {__ldg(vhf + wo + LB_K_SP * npp), __ldg(vlf + wo + LB_K_SP * npp)};
+      const F2 wS = {__ldg(vhf + wo + LB_K_S * kp), __ldg(vlf + wo + LB_K_S * kp)};
+      const F2 wSp = {__ldg(vhf + wo + LB_K_SP * kp), __ldg(vlf + wo + LB_K_SP * kp)};
       F2 wSD = {0.f, 0.f};
-      if (PASS2) wSD = {__ldg(vhf + wo + LB_K_SPPDP * npp), __ldg(vlf + wo + LB_K_SPPDP * npp)};
+      if (PASS2) wSD = {__ldg(vhf + wo + LB_K_SPPDP * kp), __ldg(vlf + wo + LB_K_SPPDP * kp)};
       F2* c = cs;
 #pragma unroll
       for (int r = 0; r < RC; ++r) {
@@ -650,11 +651,11 @@ static int run_epib(lb_ctx* c, int prec, int R, int nsplit, const double* part, 
   const float4* vh = (const float4*)c->vals_hi;
   const float4* vl = (const float4*)c->vals_lo;
   if (prec == LB_FP32)
-    k_epib<RC, PASS2, 1><<<eb, 256, 0, c->stream>>>(N, c->np, R, nsplit, part, c->nrm, c->row_ptr, c->near_patch,
-                                                     vh, nullptr, D, o0, o1, o2, o3);
+    k_epib<RC, PASS2, 1><<<eb, 256, 0, c->stream>>>(N, c->np, c->nnzb, R, nsplit, part, c->nrm, c->row_ptr,
+                                                     c->near_patch, vh, nullptr, D, o0, o1, o2, o3);
   else
-    k_epib<RC, PASS2, 2><<<eb, 256, 0, c->stream>>>(N, c->np, R, nsplit, part, c->nrm, c->row_ptr, c->near_patch,
-                                                     vh, vl, D, o0, o1, o2, o3);
+    k_epib<RC, PASS2, 2><<<eb, 256, 0, c->stream>>>(N, c->np, c->nnzb, R, nsplit, part, c->nrm, c->row_ptr,
+                                                     c->near_patch, vh, vl, D, o0, o1, o2, o3);
   LB_LAUNCH(c);
   return LB_OK;
 }
