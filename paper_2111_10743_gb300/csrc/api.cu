@@ -267,7 +267,7 @@ extern "C" int lb_destroy(lb_ctx* c) {
   free_near(c);
   for (DevBuf* b : {&c->ws_part, &c->ws_pot, &c->ws_src, &c->ws_vec, &c->ws_red, &c->ws_stage_in,
                     &c->ws_stage_out, &c->ws_gm, &c->ws_quad, &c->ws_bpot, &c->ws_bgm, &c->ws_bvec, &c->ws_dlow, &c->ws_a1,
-                    &c->ws_adj, &c->ws_shape, &c->ws_grad, &c->ws_fden})
+                    &c->ws_adj, &c->ws_shape, &c->ws_grad, &c->ws_fden, &c->ws_rec})
     if (b->p) cudaFree(b->p);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

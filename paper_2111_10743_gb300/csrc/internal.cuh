@@ -123,6 +123,7 @@ struct lb_ctx {
   // workspace
   DevBuf ws_part, ws_pot, ws_src, ws_vec, ws_red, ws_stage_in, ws_stage_out, ws_gm, ws_quad;
   DevBuf ws_bpot, ws_bgm, ws_bvec;  // batched applies and the lockstep solver
+  DevBuf ws_rec;                    // the refinement's recycled Krylov space
   DevBuf ws_dlow;                   // float32 / double-float copies of correction densities
   DevBuf ws_a1;                     // A1 apply: surface gradients and vector single layers
   DevBuf ws_adj;                    // transposed applies

@@ -308,6 +308,175 @@ static int apply_S_dev(lb_ctx* c, int prec, const double* s, double* out) {
   return LB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Recycling the first inner solve's Krylov space in the later ones of the
+// refinement (GCRO, de Sturler 1996; the augmented GMRES of Saad 1997).  The
+// first inner GMRES leaves V (k + 1 basis vectors) and, in the Hessenberg
+// storage, R with the Givens rotations Omega_j that produced it:
+// Omega_k ... Omega_1 H_k = [R; 0], so H_k = Q R with Q the first k columns
+// of Omega_1^T ... Omega_k^T.  Then C = V Q has orthonormal columns and
+// A32 U = C for U = V_k R^-1.  A later inner solve of A32 delta = r is
+// minimised over span(U) + K_m((I - C C^T) A32, r'), r' = r - C C^T r:
+// with B = C^T A32 V2 collected during its Arnoldi process,
+// delta = U (C^T r - B y) + V2 y, and its residual is that of the small
+// least-squares problem.  A restarted GMRES would rebuild the directions
+// that the first solve already found (two iterations on the benchmark
+// surface: plain float32 GMRES takes 9 iterations to 3e-11, the
+// restarted refinement 5 + 6).
+struct Recycle {
+  int k = 0;
+  double* V = nullptr;   // [k + 1][N] the first solve's basis
+  double* C = nullptr;   // [k][N] C = V Q
+  double* sm = nullptr;  // device scratch: alpha [k], B [k][max_iter], two k-vectors
+  std::vector<double> R;  // k x k upper triangle, column-major
+};
+
+// after the first inner gmres (k iterations, workspace of max_iter)
+static int recycle_capture(lb_ctx* c, int k, int max_iter, Recycle* rc) {
+  rc->k = 0;
+  if (k < 1) return LB_OK;
+  const int64_t N = c->N;
+  Gm G;
+  LB_CHECK(gm_work(c, max_iter, &G));  // the first solve's layout
+  const size_t need = (size_t)(2 * k + 1) * N + (size_t)k * (max_iter + 3) + (size_t)(k + 1) * k + 8;
+  LB_CHECK(lb_ensure(c, c->ws_rec, need * sizeof(double)));
+  rc->V = (double*)c->ws_rec.p;
+  rc->C = rc->V + (size_t)(k + 1) * N;
+  rc->sm = rc->C + (size_t)k * N;
+  double* Qd = rc->sm + (size_t)k * (max_iter + 3);
+  LB_CUDA(c, cudaMemcpyAsync(rc->V, G.V, (size_t)(k + 1) * N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  std::vector<double> Hm((size_t)G.ldh * k), cs(k), sn(k);
+  LB_CUDA(c, cudaMemcpyAsync(Hm.data(), G.Hm, Hm.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CUDA(c, cudaMemcpyAsync(cs.data(), G.cs, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CUDA(c, cudaMemcpyAsync(sn.data(), G.sn, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  rc->R.assign((size_t)k * k, 0.0);
+  for (int l = 0; l < k; ++l)
+    for (int i = 0; i <= l; ++i) rc->R[(size_t)l * k + i] = Hm[(size_t)l * G.ldh + i];
+  for (int i = 0; i < k; ++i)
+    if (!(std::fabs(rc->R[(size_t)i * k + i]) > 0)) return LB_OK;  // breakdown: no recycling
+  // Q = Omega_1^T ... Omega_k^T [I_k; 0], column-major (k + 1) x k
+  std::vector<double> Q((size_t)(k + 1) * k, 0.0);
+  for (int l = 0; l < k; ++l) Q[(size_t)l * (k + 1) + l] = 1.0;
+  for (int j = k - 1; j >= 0; --j)
+    for (int l = 0; l < k; ++l) {
+      double* q = &Q[(size_t)l * (k + 1)];
+      const double a = q[j], b = q[j + 1];
+      q[j] = cs[j] * a - sn[j] * b;
+      q[j + 1] = sn[j] * a + cs[j] * b;
+    }
+  LB_CUDA(c, cudaMemcpyAsync(Qd, Q.data(), Q.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  const unsigned nb = vec_blocks(c);
+  for (int l = 0; l < k; ++l) {
+    k_combine<<<nb, 256, 0, c->stream>>>(N, k + 1, rc->V, N, Qd + (size_t)l * (k + 1), rc->C + (size_t)l * N, 0);
+    LB_LAUNCH(c);
+  }
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));  // Q (host) is released on return
+  rc->k = k;
+  return LB_OK;
+}
+
+// GMRES for A32 x = b over span(U) + the projected Krylov space (above);
+// *res relative to |b|
+static int gmres_recycled(lb_ctx* c, const double* b, double* x, double tol, int max_iter, const Recycle& rc,
+                          int* iters, double* res) {
+  const int64_t N = c->N;
+  const int k = rc.k;
+  const unsigned nb = vec_blocks(c);
+  Gm G;
+  LB_CHECK(gm_work(c, max_iter, &G));
+  double* alpha = rc.sm;
+  double* Bm = alpha + k;                          // column j at Bm + j k
+  double* t1 = Bm + (size_t)k * max_iter;          // second projection pass
+  *iters = 0;
+  *res = 0;
+  double bb = 0;
+  LB_CHECK(dots(c, G, 1, b, b, G.scal + 2, 0));
+  LB_CHECK(read_scalar(c, G.scal + 2, &bb));
+  const double bnorm = std::sqrt(bb);
+  if (!std::isfinite(bnorm)) return lb_fail(c, LB_EINVAL, "non-finite right-hand side");
+  if (!(bnorm > 0)) {
+    LB_CUDA(c, cudaMemsetAsync(x, 0, N * sizeof(double), c->stream));
+    return LB_OK;
+  }
+  // alpha = C^T b, r' = b - C alpha (two passes)
+  LB_CUDA(c, cudaMemcpyAsync(G.w, b, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  LB_CHECK(dots(c, G, k, rc.C, G.w, alpha, 0));
+  k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, k, rc.C, N, alpha, G.w);
+  LB_LAUNCH(c);
+  LB_CHECK(dots(c, G, k, rc.C, G.w, t1, 0));
+  k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, k, rc.C, N, t1, G.w);
+  LB_LAUNCH(c);
+  k_add_small<<<lb_div_up(k, 128), 128, 0, c->stream>>>(k, t1, alpha);
+  LB_LAUNCH(c);
+  double rr2 = 0;
+  LB_CHECK(dots(c, G, 1, G.w, G.w, G.scal + 2, 0));
+  LB_CHECK(read_scalar(c, G.scal + 2, &rr2));
+  const double beta = std::sqrt(rr2);
+  int kk = 0;
+  double r = beta / bnorm;
+  if (beta > 0 && r >= tol) {
+    LB_CUDA(c, cudaMemsetAsync(G.g, 0, (G.m + 2) * sizeof(double), c->stream));
+    c->host_pinned[8] = beta;
+    LB_CUDA(c, cudaMemcpyAsync(G.g, c->host_pinned + 8, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    k_sqrt_to<<<1, 32, 0, c->stream>>>(G.scal + 2, G.scal + 3);
+    LB_LAUNCH(c);
+    k_scale_by<<<nb, 256, 0, c->stream>>>(N, G.w, G.scal + 3, G.V);
+    LB_LAUNCH(c);
+    for (int j = 0; j < max_iter; ++j) {
+      const double* vj = G.V + (int64_t)j * G.ldv;
+      LB_CHECK(lb_apply_op(c, c->params.formulation, LB_FP32, vj, G.w));
+      double* bj = Bm + (size_t)j * k;
+      LB_CHECK(dots(c, G, k, rc.C, G.w, bj, 0));
+      k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, k, rc.C, N, bj, G.w);
+      LB_LAUNCH(c);
+      LB_CHECK(dots(c, G, k, rc.C, G.w, t1, 0));
+      k_axpy_multi<<<nb, 256, 0, c->stream>>>(N, k, rc.C, N, t1, G.w);
+      LB_LAUNCH(c);
+      k_add_small<<<lb_div_up(k, 128), 128, 0, c->stream>>>(k, t1, bj);
+      LB_LAUNCH(c);
+      LB_CHECK(arnoldi_step(c, G, j, beta));
+      double rj = 0;
+      LB_CHECK(read_scalar(c, G.scal, &rj));
+      kk = j + 1;
+      r = rj * beta / bnorm;
+      if (!std::isfinite(r)) return lb_fail(c, LB_EINVAL, "GMRES breakdown: non-finite residual");
+      if (r < tol || rj == 0.0) break;
+    }
+    k_backsolve<<<1, 32, 0, c->stream>>>(kk, G.ldh, G.Hm, G.g, G.y);
+    LB_LAUNCH(c);
+  }
+  // z = alpha - B y, coefficients of V_k: R^-1 z
+  std::vector<double> al(k), Bh((size_t)k * std::max(kk, 1)), yh(std::max(kk, 1)), cu(k);
+  LB_CUDA(c, cudaMemcpyAsync(al.data(), alpha, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (kk > 0) {
+    LB_CUDA(c, cudaMemcpyAsync(Bh.data(), Bm, (size_t)k * kk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(yh.data(), G.y, kk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < k; ++i) {
+    double z = al[i];
+    for (int j = 0; j < kk; ++j) z -= Bh[(size_t)j * k + i] * yh[j];
+    cu[i] = z;
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double s = cu[i];
+    for (int l = i + 1; l < k; ++l) s -= rc.R[(size_t)l * k + i] * cu[l];
+    cu[i] = s / rc.R[(size_t)i * k + i];
+  }
+  LB_CUDA(c, cudaMemcpyAsync(t1, cu.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  k_combine<<<nb, 256, 0, c->stream>>>(N, k, rc.V, N, t1, x, 0);
+  LB_LAUNCH(c);
+  if (kk > 0) {
+    k_combine<<<nb, 256, 0, c->stream>>>(N, kk, G.V, G.ldv, G.y, x, 1);
+    LB_LAUNCH(c);
+  }
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));  // host vectors are released on return
+  *iters = kk;
+  *res = r;
+  return LB_OK;
+}
+
 // one right-hand side: b (device) -> sigma (device).  In the refined mode the
 // solution potential u is produced here too (u_out), otherwise by the caller.
 //
@@ -354,6 +523,7 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
     bool ok = nbv == 0.0;
     int steps = 0;
     double rel = nbv == 0.0 ? 0.0 : 1.0;
+    Recycle rec;
     if (first) hist.push_back(1.0);
     for (int s = 0; s < p.max_refine && !ok; ++s) {
       int its = 0;
@@ -361,7 +531,11 @@ static int solve_one(lb_ctx* c, const double* b, double* sigma, double* scratch,
       // once the residual r_s is known (rel = |r_s| / |b|), the inner solve
       // need only take it to half the target: tol |b| / 2
       const double itol = s == 0 ? p.inner_tol : std::max(p.inner_tol, std::min(0.5, 0.5 * p.tol / rel));
-      LB_CHECK(gmres(c, LB_FP32, r, delta, itol, p.max_iter, &its, &ires, nullptr));
+      if (s > 0 && rec.k > 0)
+        LB_CHECK(gmres_recycled(c, r, delta, itol, p.max_iter, rec, &its, &ires));
+      else
+        LB_CHECK(gmres(c, LB_FP32, r, delta, itol, p.max_iter, &its, &ires, nullptr));
+      if (s == 0) LB_CHECK(recycle_capture(c, its, p.max_iter, &rec));
       it += its;
       k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, delta, 1.0, sigma);
       LB_LAUNCH(c);
