@@ -619,6 +619,15 @@ struct LkDev {
   double* partial;     // [R][m+2][GM_RB]
   int* jdev;           // iteration index
   double* resbuf;      // [R] residual estimates of the active systems, in act order
+  // recycled first-stage spaces (refinement; null when off): for system r,
+  // ck[r] vectors C at C + coff[r] (stride N), B = C^T A V2 columns at
+  // Bm + r * bld + j * kmax, a second-pass scratch at Bm + r * bld + m * kmax
+  const double* C = nullptr;
+  const int64_t* coff = nullptr;
+  const int* ck = nullptr;
+  double* Bm = nullptr;
+  int64_t bld = 0;
+  int kmax = 0;
 };
 
 // offsets inside a system's small block
@@ -694,6 +703,84 @@ __global__ void k_lk_addsmall(LkDev d, LkAct act) {
   if (v > *d.jdev) return;
   double* sm = d.small + (int64_t)r * d.SM;
   sm[LK_H(d) + v] += sm[LK_Y(d) + v];
+}
+
+// partial dot products of w_a with system r's recycled vectors C_r
+__global__ void k_lk_cdots(LkDev d, LkAct act, const double* __restrict__ W) {
+  __shared__ double sh[256];
+  const int a = blockIdx.y, r = act.r[a];
+  const double* w = W + (int64_t)a * d.N;
+  const int nvec = d.ck[r];
+  for (int v = 0; v < nvec; ++v) {
+    const double* x = d.C + d.coff[r] + (int64_t)v * d.N;
+    double s = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * blockDim.x)
+      s += x[i] * w[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+      if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) d.partial[((int64_t)a * (d.m + 2) + v) * gridDim.x + blockIdx.x] = sh[0];
+    __syncthreads();
+  }
+}
+
+// column `slot` of system r's coefficient block (slot < 0: the current
+// iteration's B column j; m: a scratch column; m + 1: alpha = C^T b)
+__device__ __forceinline__ double* lk_ccol(const LkDev& d, int r, int slot) {
+  return d.Bm + (int64_t)r * d.bld + (int64_t)(slot < 0 ? *d.jdev : slot) * d.kmax;
+}
+
+// column `slot` = ordered sums of the partials of k_lk_cdots
+__global__ void k_lk_creduce(LkDev d, LkAct act, int slot, int nblk) {
+  const int a = blockIdx.y, r = act.r[a];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.ck[r]) return;
+  double s = 0;
+  for (int b = 0; b < nblk; ++b) s += d.partial[((int64_t)a * (d.m + 2) + v) * nblk + b];
+  lk_ccol(d, r, slot)[v] = s;
+}
+
+// w_a -= C_r (column `slot`)
+__global__ void k_lk_caxpy(LkDev d, LkAct act, double* __restrict__ W, int slot) {
+  const int a = blockIdx.y, r = act.r[a];
+  const int nvec = d.ck[r];
+  const double* coef = lk_ccol(d, r, slot);
+  double* w = W + (int64_t)a * d.N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.N; i += (int64_t)gridDim.x * blockDim.x) {
+    double s2 = w[i];
+    for (int v = 0; v < nvec; ++v) s2 -= coef[v] * d.C[d.coff[r] + (int64_t)v * d.N + i];
+    w[i] = s2;
+  }
+}
+
+// column `dst` += column `src`
+__global__ void k_lk_cadd(LkDev d, LkAct act, int dst, int src) {
+  const int a = blockIdx.y, r = act.r[a];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= d.ck[r]) return;
+  lk_ccol(d, r, dst)[v] += lk_ccol(d, r, src)[v];
+}
+
+// W_a -= C_r (C_r^T W_a) in two passes, the coefficients summed into
+// column `slot` of system r's block
+static int lk_project(lb_ctx* c, const LkDev& d, const LkAct& act, double* W, int slot) {
+  const unsigned nb = vec_blocks(c);
+  const dim3 gv(nb, act.n), gd(GM_RB, act.n), gc(lb_div_up(d.kmax, 64), act.n);
+  for (int pass = 0; pass < 2; ++pass) {
+    const int dst = pass == 0 ? slot : d.m;
+    k_lk_cdots<<<gd, 256, 0, c->stream>>>(d, act, W);
+    LB_LAUNCH(c);
+    k_lk_creduce<<<gc, 64, 0, c->stream>>>(d, act, dst, GM_RB);
+    LB_LAUNCH(c);
+    k_lk_caxpy<<<gv, 256, 0, c->stream>>>(d, act, W, dst);
+    LB_LAUNCH(c);
+  }
+  k_lk_cadd<<<gc, 64, 0, c->stream>>>(d, act, slot, d.m);
+  LB_LAUNCH(c);
+  return LB_OK;
 }
 
 // h_{j+1} = |w|, V_r[j+1] = w / |w| (zero when |w| = 0)
@@ -865,6 +952,7 @@ static int lk_iteration(lb_ctx* c, Lockstep& L, int prec, const LkAct& act) {
   k_lk_gather<<<gv, 256, 0, c->stream>>>(d, act, L.in);
   LB_LAUNCH(c);
   LB_CHECK(lb_apply_a3_batch(c, prec, act.n, L.in, L.out, nullptr));
+  if (d.C) LB_CHECK(lk_project(c, d, act, L.out, -1));  // recycled spaces: B column j = C^T w
   // classical Gram-Schmidt, twice: h = V^T w, w -= V h, y = V^T w, w -= V y, h += y
   k_lk_dots<<<gd, 256, 0, c->stream>>>(d, act, L.out, 0);
   LB_LAUNCH(c);
@@ -978,7 +1066,8 @@ static void lk_replay_profile(lb_ctx* c, const LkGraph& g) {
 
 // GMRES on R systems at once: b, x [R][N]; systems with b = 0 get x = 0
 static int gmres_lockstep(lb_ctx* c, Lockstep& L, int prec, const double* b, double* x, double tol, int max_iter,
-                          std::vector<int>* its, std::vector<double>* res, std::vector<double>* hist0) {
+                          std::vector<int>* its, std::vector<double>* res, std::vector<double>* hist0,
+                          const std::vector<double>* tolscale = nullptr) {
   const int64_t N = c->N;
   const int R = L.R;
   const LkDev d = L.d;
@@ -1035,7 +1124,7 @@ static int gmres_lockstep(lb_ctx* c, Lockstep& L, int prec, const double* b, dou
       (*its)[r] = j + 1;
       (*res)[r] = rr;
       if (hist0 && r == 0) hist0->push_back(rr);
-      if (!(rr < tol || rr == 0.0)) next.push_back(r);
+      if (!(rr < tol * (tolscale ? (*tolscale)[r] : 1.0) || rr == 0.0)) next.push_back(r);
     }
     act.swap(next);
   }
@@ -1046,6 +1135,167 @@ static int gmres_lockstep(lb_ctx* c, Lockstep& L, int prec, const double* b, dou
     k_combine<<<nb, 256, 0, c->stream>>>(N, (*its)[r], d.V + (int64_t)r * N, (int64_t)R * N,
                                          d.small + (int64_t)r * d.SM + LK_Y(d), x + (int64_t)r * N, 0);
     LB_LAUNCH(c);
+  }
+  return LB_OK;
+}
+
+// The lockstep refinement recycles each system's first inner Krylov space
+// as the single solve does (recycle_capture, gmres_recycled): per original
+// system its basis V (k + 1 vectors), C = V Q (k vectors) and R, kept in
+// ws_rec for the later stages, whose batched iterations project every new
+// vector against C (lk_project) and record B = C^T A V2.
+struct LkRecycle {
+  int R = 0, m = 0, kmax = 0;
+  std::vector<int> k;          // per original system, 0: nothing recycled
+  std::vector<int64_t> voff;   // offsets of V and C in ws_rec
+  std::vector<int64_t> coff;
+  std::vector<std::vector<double>> Rm;  // k x k upper triangles, column-major
+  double* base = nullptr;
+  int64_t* dcoff = nullptr;    // device: per stage-2 system
+  int* dck = nullptr;
+  double* Bm = nullptr;        // device: per stage-2 system (m + 2) kmax coefficients
+  double* coef = nullptr;      // device: kmax closing coefficients
+};
+
+// after the first lockstep stage of the systems act (stage index a ~ act[a])
+static int lk_recycle_capture(lb_ctx* c, Lockstep& La, const std::vector<int>& act, const std::vector<int>& its,
+                              int R, int m, LkRecycle* rc) {
+  const int64_t N = c->N;
+  const int Ra = (int)act.size();
+  rc->R = R;
+  rc->m = m;
+  rc->k.assign(R, 0);
+  rc->voff.assign(R, 0);
+  rc->coff.assign(R, 0);
+  rc->Rm.assign(R, {});
+  int64_t tot = 0;
+  int kmax = 1;
+  for (int a = 0; a < Ra; ++a) {
+    tot += (int64_t)(2 * its[a] + 1) * N;
+    kmax = std::max(kmax, its[a]);
+  }
+  rc->kmax = kmax;
+  // layout (doubles): V and C of every system [tot], Q [qn], the closing
+  // coefficients [kmax], the stage blocks [R (m + 2) kmax], then R int64
+  // offsets and R ints
+  const int64_t qn = (int64_t)(kmax + 1) * kmax;
+  const size_t need = (size_t)tot + (size_t)qn + (size_t)kmax + (size_t)R * (m + 2) * kmax + (size_t)R * 2 + 16;
+  LB_CHECK(lb_ensure(c, c->ws_rec, need * sizeof(double)));
+  double* p = (double*)c->ws_rec.p;
+  rc->base = p;
+  double* Qd = p + tot;
+  rc->coef = Qd + qn;
+  rc->Bm = rc->coef + kmax;
+  rc->dcoff = (int64_t*)(rc->Bm + (size_t)R * (m + 2) * kmax);
+  rc->dck = (int*)(rc->dcoff + R);
+  const LkDev& d = La.d;
+  const unsigned nb = vec_blocks(c);
+  int64_t off = 0;
+  std::vector<double> small(d.SM);
+  for (int a = 0; a < Ra; ++a) {
+    const int k = its[a], r = act[a];
+    if (k < 1) continue;
+    LB_CUDA(c, cudaMemcpyAsync(small.data(), d.small + (int64_t)a * d.SM, d.SM * sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double* Hm = small.data() + LK_HM(d);
+    const double* cs = small.data() + LK_CS(d);
+    const double* sn = small.data() + LK_SN(d);
+    std::vector<double> Rk((size_t)k * k, 0.0);
+    bool ok = true;
+    for (int l = 0; l < k; ++l)
+      for (int i = 0; i <= l; ++i) Rk[(size_t)l * k + i] = Hm[(size_t)l * d.ldh + i];
+    for (int i = 0; i < k; ++i) ok = ok && std::fabs(Rk[(size_t)i * k + i]) > 0;
+    if (!ok) continue;  // breakdown: this system restarts plainly
+    std::vector<double> Q((size_t)(k + 1) * k, 0.0);
+    for (int l = 0; l < k; ++l) Q[(size_t)l * (k + 1) + l] = 1.0;
+    for (int j = k - 1; j >= 0; --j)
+      for (int l = 0; l < k; ++l) {
+        double* q = &Q[(size_t)l * (k + 1)];
+        const double x0 = q[j], x1 = q[j + 1];
+        q[j] = cs[j] * x0 - sn[j] * x1;
+        q[j + 1] = sn[j] * x0 + cs[j] * x1;
+      }
+    double* V = p + off;
+    double* C = V + (int64_t)(k + 1) * N;
+    for (int v = 0; v <= k; ++v)
+      LB_CUDA(c, cudaMemcpyAsync(V + (int64_t)v * N, d.V + ((int64_t)v * d.R + a) * N, N * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    LB_CUDA(c, cudaMemcpyAsync(Qd, Q.data(), Q.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    for (int l = 0; l < k; ++l) {
+      k_combine<<<nb, 256, 0, c->stream>>>(N, k + 1, V, N, Qd + (size_t)l * (k + 1), C + (int64_t)l * N, 0);
+      LB_LAUNCH(c);
+    }
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));  // Q (host) is reused for the next system
+    rc->k[r] = k;
+    rc->voff[r] = off;
+    rc->coff[r] = off + (int64_t)(k + 1) * N;
+    rc->Rm[r] = std::move(Rk);
+    off += (int64_t)(2 * k + 1) * N;
+  }
+  return LB_OK;
+}
+
+// attach the recycled spaces of the systems act to a stage's lockstep; false
+// when one of them has none (that stage then restarts plainly)
+static int lk_recycle_attach(lb_ctx* c, const LkRecycle& rc, const std::vector<int>& act, Lockstep& La, bool* on) {
+  *on = false;
+  if (rc.k.empty()) return LB_OK;
+  for (int r : act)
+    if (rc.k[r] < 1) return LB_OK;
+  const int Ra = (int)act.size();
+  std::vector<int64_t> co(Ra);
+  std::vector<int> ck(Ra);
+  for (int a = 0; a < Ra; ++a) {
+    co[a] = rc.coff[act[a]];
+    ck[a] = rc.k[act[a]];
+  }
+  LB_CUDA(c, cudaMemcpyAsync(rc.dcoff, co.data(), Ra * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  LB_CUDA(c, cudaMemcpyAsync(rc.dck, ck.data(), Ra * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  LB_CUDA(c, cudaStreamSynchronize(c->stream));
+  LkDev& d = La.d;
+  d.C = rc.base;
+  d.coff = rc.dcoff;
+  d.ck = rc.dck;
+  d.Bm = rc.Bm;
+  d.kmax = rc.kmax;
+  d.bld = (int64_t)(d.m + 2) * rc.kmax;
+  *on = true;
+  return LB_OK;
+}
+
+// x_a += V_a R_a^-1 (alpha_a - B_a y_a) for every system of a recycled stage
+static int lk_recycle_close(lb_ctx* c, const LkRecycle& rc, const std::vector<int>& act, Lockstep& La,
+                            const std::vector<int>& its, double* x) {
+  const int64_t N = c->N;
+  const LkDev& d = La.d;
+  const unsigned nb = vec_blocks(c);
+  double* coef = rc.coef;
+  for (size_t a = 0; a < act.size(); ++a) {
+    const int r = act[a], k = rc.k[r], kk = its[a];
+    std::vector<double> blk((size_t)d.bld), y(std::max(kk, 1)), cu(k);
+    LB_CUDA(c, cudaMemcpyAsync(blk.data(), rc.Bm + (int64_t)a * d.bld, d.bld * sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream));
+    if (kk > 0)
+      LB_CUDA(c, cudaMemcpyAsync(y.data(), d.small + (int64_t)a * d.SM + LK_Y(d), kk * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double* alpha = blk.data() + (size_t)(d.m + 1) * d.kmax;
+    for (int i = 0; i < k; ++i) {
+      double z = alpha[i];
+      for (int j = 0; j < kk; ++j) z -= blk[(size_t)j * d.kmax + i] * y[j];
+      cu[i] = z;
+    }
+    const std::vector<double>& Rk = rc.Rm[r];
+    for (int i = k - 1; i >= 0; --i) {
+      double sum = cu[i];
+      for (int l = i + 1; l < k; ++l) sum -= Rk[(size_t)l * k + i] * cu[l];
+      cu[i] = sum / Rk[(size_t)i * k + i];
+    }
+    LB_CUDA(c, cudaMemcpyAsync(coef, cu.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    k_combine<<<nb, 256, 0, c->stream>>>(N, k, rc.base + rc.voff[r], N, coef, x + (int64_t)a * N, 1);
+    LB_LAUNCH(c);
+    LB_CUDA(c, cudaStreamSynchronize(c->stream));  // cu (host) is reused
   }
   return LB_OK;
 }
@@ -1099,12 +1349,31 @@ static int solve_lockstep(lb_ctx* c, int R, const double* b, double* sigma, doub
       if (nbv[k] != 0.0) { act.push_back(k); rel[k] = 1.0; }
     }
     if (R > 0 && nbv[0] != 0.0) hist.push_back(1.0);
+    LkRecycle rec;
     for (int s = 0; s < p.max_refine && !act.empty(); ++s) {
       const int Ra = (int)act.size();
       LB_CHECK(gather_rows(c, r, act, rin));
       Lockstep La;
       LB_CHECK(lockstep_work(c, Ra, p.max_iter, &La));
-      LB_CHECK(gmres_lockstep(c, La, LB_FP32, rin, delta, p.inner_tol, p.max_iter, &its, &res, nullptr));
+      bool recycled = false;
+      if (s > 0) LB_CHECK(lk_recycle_attach(c, rec, act, La, &recycled));
+      if (recycled) {
+        // project the residuals off C (alpha = C^T r into slot m + 1); the
+        // inner tolerance stays relative to the unprojected |r|
+        std::vector<int> idx(Ra);
+        for (int a = 0; a < Ra; ++a) idx[a] = a;
+        std::vector<double> before, after;
+        LB_CHECK(lk_norms(c, La, rin, idx, &before));
+        LB_CHECK(lk_project(c, La.d, make_act(idx), rin, La.d.m + 1));
+        LB_CHECK(lk_norms(c, La, rin, idx, &after));
+        std::vector<double> scale(Ra, 1.0);
+        for (int a = 0; a < Ra; ++a) scale[a] = after[a] > 0 ? before[a] / after[a] : 1.0;
+        LB_CHECK(gmres_lockstep(c, La, LB_FP32, rin, delta, p.inner_tol, p.max_iter, &its, &res, nullptr, &scale));
+        LB_CHECK(lk_recycle_close(c, rec, act, La, its, delta));
+      } else {
+        LB_CHECK(gmres_lockstep(c, La, LB_FP32, rin, delta, p.inner_tol, p.max_iter, &its, &res, nullptr));
+      }
+      if (s == 0) LB_CHECK(lk_recycle_capture(c, La, act, its, R, p.max_iter, &rec));
       for (int a = 0; a < Ra; ++a) {
         itsum[act[a]] += its[a];
         k_axpby<<<nb, 256, 0, c->stream>>>(N, 1.0, delta + (int64_t)a * N, 1.0, sigma + (int64_t)act[a] * N);
