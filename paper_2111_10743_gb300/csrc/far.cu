@@ -1080,8 +1080,12 @@ __device__ __forceinline__ double to_d(F2 v) { return df_to_double(v); }
 // moves four nodes' weights and densities with single 16-byte loads; the
 // weights are kernel-major (plane k at k * sp.kplane vectors), so that a
 // row's blocks of one kernel are contiguous; four vectors per lane in flight.
+// A row's loads form a chain (row offsets, near patches, weights, far sums),
+// so the kernel is bound by latency: the float32 form is held to 40
+// registers (six 256-thread CTAs, 48 warps per SM) to keep more rows in
+// flight; the float64 and double-float forms would spill at that bound.
 template <int MODE>
-__global__ void k_epilogue(int64_t N, int np, int npv, int nsplit, int nacc, const double* __restrict__ part,
+__global__ void __launch_bounds__(256, MODE == 1 ? 6 : 0) k_epilogue(int64_t N, int np, int npv, int nsplit, int nacc, const double* __restrict__ part,
                            const double* __restrict__ nrm, const int64_t* __restrict__ row_ptr,
                            const int32_t* __restrict__ near_patch, const double* __restrict__ vals,
                            const float4* __restrict__ vh, const float4* __restrict__ vl, EpiSpec sp) {
